@@ -1,0 +1,161 @@
+"""Seeded synthetic particle systems (inputs only; no Ewald/SE arithmetic).
+
+This module is shared by the tests, the oracle checks and the benchmark.  It
+draws positions and charges and holds the named workload parameters; it
+computes nothing of the method itself.
+
+* ``uniform_charges`` -- N point charges i.i.d. uniform in [0, L)^3 with
+  charges +1, -1 alternating (neutral for even N), the uniform test systems of
+  Sec. 4 and 6 (N/L^3 about 100 in Sec. 6).
+* ``water_box`` -- an SPC/E-like water box standing in for the equilibrated
+  water systems of Sec. 6-9 (q_O = -0.8476, q_H = +0.4238, 0.1 nm O-H bonds,
+  109.47 degree H-O-H angle, 33.4 molecules per nm^3, i.e. about 100 atoms per
+  nm^3).  Molecules sit on a jittered cubic lattice with uniformly random
+  orientations.  The paper's own coordinates are not available; these are
+  synthetic stand-ins with the same charges, geometry and density.
+* ``nacl_cell`` -- the 8-ion rock-salt conventional cell.
+* ``ensemble`` -- independent water boxes with L uniform in [3, 7] nm.
+"""
+import math
+
+import numpy as np
+
+Q_O = -0.8476
+Q_H = 0.4238
+R_OH = 0.1                      # nm
+THETA_HOH = 109.47              # degrees
+WATER_DENSITY = 33.4            # molecules / nm^3
+
+
+def uniform_charges(N, L, seed=1, dtype=np.float64):
+    """N charges uniform in [0, L)^3, q = +1, -1, +1, ... (PCG64(seed))."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = rng.uniform(0.0, L, size=(N, 3))
+    q = np.where(np.arange(N) % 2 == 0, 1.0, -1.0)
+    x = x.astype(dtype)
+    # a coordinate that rounded up to L in a narrower type is put back in range
+    x[x >= dtype(L)] = 0
+    return x, q.astype(dtype)
+
+
+def _random_rotations(rng, n):
+    """n uniformly random rotation matrices (Shoemake's quaternion method)."""
+    u1, u2, u3 = rng.uniform(size=(3, n))
+    a, b = np.sqrt(1.0 - u1), np.sqrt(u1)
+    qw = a * np.sin(2 * np.pi * u2)
+    qx = a * np.cos(2 * np.pi * u2)
+    qy = b * np.sin(2 * np.pi * u3)
+    qz = b * np.cos(2 * np.pi * u3)
+    R = np.empty((n, 3, 3))
+    R[:, 0, 0] = 1 - 2 * (qy * qy + qz * qz)
+    R[:, 0, 1] = 2 * (qx * qy - qz * qw)
+    R[:, 0, 2] = 2 * (qx * qz + qy * qw)
+    R[:, 1, 0] = 2 * (qx * qy + qz * qw)
+    R[:, 1, 1] = 1 - 2 * (qx * qx + qz * qz)
+    R[:, 1, 2] = 2 * (qy * qz - qx * qw)
+    R[:, 2, 0] = 2 * (qx * qz - qy * qw)
+    R[:, 2, 1] = 2 * (qy * qz + qx * qw)
+    R[:, 2, 2] = 1 - 2 * (qx * qx + qy * qy)
+    return R
+
+
+def water_box(L, seed=2, dtype=np.float64, density=WATER_DENSITY, jitter=0.05):
+    """SPC/E-like water box of side L (nm); atoms ordered O, H, H per molecule.
+
+    n_mol = round(density L^3) molecules on n_mol sites drawn without
+    replacement from a cubic lattice of ceil(n_mol^(1/3))^3 sites, each oxygen
+    jittered uniformly by +-jitter nm per axis, each molecule randomly rotated.
+    Returns (x [3 n_mol, 3], q [3 n_mol]); exactly neutral in float32 and
+    float64 since q_O = -2 q_H exactly in binary too."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n_mol = int(round(density * L ** 3))
+    ns = int(math.ceil(n_mol ** (1.0 / 3.0) - 1e-12))
+    a = L / ns
+    sites = rng.choice(ns ** 3, size=n_mol, replace=False)
+    ijk = np.stack([sites // (ns * ns), (sites // ns) % ns, sites % ns], axis=1)
+    O = (ijk + 0.5) * a + rng.uniform(-jitter, jitter, size=(n_mol, 3))
+    half = math.radians(THETA_HOH) / 2.0
+    # molecular frame: bisector along +z, H atoms in the xz plane
+    h1 = np.array([math.sin(half), 0.0, math.cos(half)]) * R_OH
+    h2 = np.array([-math.sin(half), 0.0, math.cos(half)]) * R_OH
+    R = _random_rotations(rng, n_mol)
+    H1 = O + R @ h1
+    H2 = O + R @ h2
+    x = np.stack([O, H1, H2], axis=1).reshape(-1, 3)
+    x = x - L * np.floor(x / L)
+    x[x >= L] = 0.0
+    q = np.tile(np.array([Q_O, Q_H, Q_H]), n_mol)
+    x = x.astype(dtype)
+    x[x >= dtype(L)] = 0
+    return x, q.astype(dtype)
+
+
+def nacl_cell(a=1.0):
+    """Rock-salt conventional cell of side a: 4 Na+ (q=+1), 4 Cl- (q=-1)."""
+    na = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]])
+    cl = np.array([[.5, 0, 0], [0, .5, 0], [0, 0, .5], [.5, .5, .5]])
+    x = np.concatenate([na, cl]) * a
+    q = np.array([1.0] * 4 + [-1.0] * 4)
+    return x, q
+
+
+def smooth7(n):
+    """Smallest integer >= n whose prime factors are all <= 7."""
+    m = max(1, int(n))
+    while True:
+        r = m
+        for p in (2, 3, 5, 7):
+            while r % p == 0:
+                r //= p
+        if r == 1:
+            return m
+        m += 1
+
+
+def ensemble(S=64, Lmin=3.0, Lmax=7.0, spacing=0.12, seed_L=999, seed0=1000,
+             dtype=np.float32):
+    """S independent water boxes; L_s ~ U[Lmin, Lmax] (PCG64(seed_L)), system s
+    from water_box(L_s, seed0 + s), grid M_s = smooth7(ceil(L_s / spacing))."""
+    rng = np.random.Generator(np.random.PCG64(seed_L))
+    Ls = rng.uniform(Lmin, Lmax, size=S)
+    out = []
+    for s, L in enumerate(Ls):
+        x, q = water_box(float(L), seed=seed0 + s, dtype=dtype)
+        M = smooth7(math.ceil(L / spacing))
+        out.append(dict(L=float(L), M=M, x=x, q=q))
+    return out
+
+
+# Named workloads: box, Ewald parameter, grid, support, precision.
+WORKLOADS = {
+    "uniform-1000-L3-M32-P16-fp64": dict(
+        kind="uniform", N=1000, L=3.0, xi=3.5, M=32, P=16, prec="fp64", seed=1,
+        target_rel_force_err=1e-8),
+    "water-L6-M52-P6-fp32comp": dict(
+        kind="water", L=6.0, xi=3.12, M=52, P=6, prec="fp32comp", seed=2,
+        target_rel_force_err=1e-3),
+    "water-L6-M96-P24-fp64": dict(
+        kind="water", L=6.0, xi=3.12, M=96, P=24, prec="fp64", seed=2,
+        target_rel_force_err=1e-10),
+    "water-L10-M84-P8-fp32comp": dict(
+        kind="water", L=10.0, xi=3.12, M=84, P=8, prec="fp32comp", seed=4,
+        target_rel_force_err=1e-4),
+    "ensemble-64-water-L3to7-P8-fp32comp": dict(
+        kind="ensemble", S=64, xi=3.12, P=8, prec="fp32comp", spacing=0.12,
+        target_rel_force_err=1e-4),
+}
+
+
+def make(name, dtype=None):
+    """(x, q, params) of a named single-system workload."""
+    w = dict(WORKLOADS[name])
+    if dtype is None:
+        dtype = np.float64 if w["prec"] == "fp64" else np.float32
+    if w["kind"] == "uniform":
+        x, q = uniform_charges(w["N"], w["L"], seed=w["seed"], dtype=dtype)
+    elif w["kind"] == "water":
+        x, q = water_box(w["L"], seed=w["seed"], dtype=dtype)
+    else:
+        raise ValueError("use ensemble() for %s" % name)
+    w["N"] = len(q)
+    return x, q, w
