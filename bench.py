@@ -1,0 +1,403 @@
+#!/usr/bin/env python3
+"""Benchmark of the SE k-space path: energy+force evaluations per second.
+
+One step = one whole k-space evaluation (bin, spread, FFT, scale, inverse
+FFT, gather; energy, forces and potentials) of the named workload, with the
+inputs resident on the GPU.  Between timed steps L2 is flushed by writing a
+256 MiB buffer (outside the timed events).  `e2e` times the same evaluation
+through the host-buffer entry point (se_energy_force_host: copies in, compute,
+copies out).  The accuracy is the relative rms force error against a
+high-accuracy FP64 evaluation on the GPU (P = 24, M ~ 4 xi L), which the tests
+pin to the direct Ewald sum.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
+
+With torchrun (N > 1) every rank evaluates its own replica of the workload
+(the path does not shard a single system); value = all ranks' evaluations per
+second of the slowest rank.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+DEFAULT_WORKLOAD = "water-L6-M52-P6-fp32comp"
+METRIC = "SE k-space energy+force evals/s and ns/atom at stated rms force error vs FP64"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+FP64_PEAK_TFLOPS = 1.25                              # nominal GB300 FP64
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="bounded CPU work of the cpu_baseline leg")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip accuracy, e2e, at-target and cpu_baseline legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def workload(name):
+    from paper_1712_04718_gb300 import systems
+    x, q, w = systems.make(name)
+    prec = "fp64" if w["prec"] == "fp64" else "fp32"
+    return x, q, w, prec
+
+
+def stage_work(w, prec, N):
+    """Algorithmic work of each own kernel per launch: (kind, amount).
+    spread: N P^3 weights, each a multiply and an add (2 flops);
+    gather: N P^3 grid values, each two FMAs (4 flops);
+    scale: complex grid read+write and the FP64 G table (bytes);
+    bin/scatter: particle bytes moved."""
+    P, M = w["P"], w["M"]
+    ts = 8 if prec == "fp64" else 4
+    nc = M * M * (M // 2 + 1)
+    return {
+        "spread": ("flop", 2.0 * N * P ** 3),
+        "gather": ("flop", 4.0 * N * P ** 3),
+        "scale": ("byte", nc * (4 * ts + 8) + M ** 3 * ts),
+        "bin": ("byte", N * (4 * ts + 8)),
+        "scatter": ("byte", N * (4 * ts + 4 * ts + 8 + 4)),
+    }
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    from paper_1712_04718_gb300 import se
+
+    x, q, w, prec = workload(args.workload)
+    N = len(q)
+    plan = se.Plan(N, w["L"], w["xi"], w["M"], w["P"], precision=prec)
+    dt = plan.dtype
+    xd = torch.tensor(x, dtype=dt, device="cuda")
+    qd = torch.tensor(q, dtype=dt, device="cuda")
+    F = torch.empty((N, 3), dtype=dt, device="cuda")
+    phi = torch.empty((N,), dtype=dt, device="cuda")
+    Ed = torch.zeros(1, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def step():
+        plan.evaluate(xd, qd, F, phi, Ed)
+
+    for _ in range(max(3, args.warmup)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    plan.get_timing(reset=True)
+    plan.set_timing(True)
+    K = args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for i in range(K):
+        flush.zero_()
+        starts[i].record()
+        step()
+        ends[i].record()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    plan.set_timing(False)
+    stages, nstage = plan.get_timing(reset=True)
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = t.item()
+    ms_step = total_ms / K
+    value = ws * K / (total_ms / 1e3)
+
+    # roofline of the dominant own kernel (average launch duration from events)
+    work = stage_work(w, prec, N)
+    per_launch_ms = {k: v / max(1, nstage) for k, v in stages.items()}
+    own = ["bin", "scatter", "spread", "scale", "gather"]
+    dom = max(own, key=lambda k: per_launch_ms[k])
+    kind, amount = work[dom]
+    secs = per_launch_ms[dom] / 1e3
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    if kind == "flop":
+        pk = FP64_PEAK_TFLOPS if prec == "fp64" else FP32_PEAK_TFLOPS
+        achieved = amount / secs / 1e12
+        roof = {"bound": "alu", "kernel": "k_" + dom, "achieved": achieved, "peak": pk,
+                "unit": "TFLOP/s", "frac": achieved / pk, "traffic": None,
+                "peak_source": ("nominal FP64" if prec == "fp64" else
+                                "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"),
+                "work_per_launch": amount}
+    else:
+        pk = peaks.get("hbm_gbs", 6800.0)
+        achieved = amount / secs / 1e9
+        roof = {"bound": "hbm", "kernel": "k_" + dom, "achieved": achieved, "peak": pk,
+                "unit": "GB/s", "frac": achieved / pk, "traffic": None,
+                "peak_source": "measured" if peaks else "fallback", "work_per_launch": amount}
+    roof["launch_us"] = per_launch_ms[dom] * 1e3
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms_step,
+        "ns_per_atom": ms_step * 1e6 / N, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "N": N, "L": w["L"], "xi": w["xi"], "M": w["M"],
+                   "P": w["P"], "precision": w["prec"], "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "flushed between steps (256 MiB write, untimed)"},
+        "stages_us_per_eval": {k: v / max(1, nstage) * 1e3 for k, v in stages.items()},
+        "fft_us_per_eval": (stages["fft_fwd"] + stages["fft_inv"]) / max(1, nstage) * 1e3,
+        "roofline": roof,
+        "gpu_launches": 5 * K,
+        "gpu_launches_note": "own kernels (bin, scatter, spread, scale, gather) per step; cuFFT kernels not counted",
+        "clocks": clk,
+    }
+
+    if rank == 0 and not args.no_extras:
+        out["accuracy"] = accuracy(se, torch, x, q, w, prec, F)
+        out["e2e"] = e2e(se, torch, x, q, w, prec, max(20, min(K, 500)))
+        if args.workload == DEFAULT_WORKLOAD:
+            out["at_target"] = at_target(se, torch, x, q, w, prec, K, flush)
+        out["cpu_baseline"] = cpu_baseline(x, q, w, args.cpu_seconds)
+    plan.close()
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def reference_forces(se, torch, x, q, w):
+    """High-accuracy FP64 SE on the GPU: P = 24, M = 2 ceil(6.2 xi L / pi)."""
+    M = 2 * math.ceil(6.2 * w["xi"] * w["L"] / math.pi)
+    plan = se.Plan(len(q), w["L"], w["xi"], M, 24, precision="fp64")
+    E, F, _ = plan.energy_force(torch.tensor(np.asarray(x, np.float64), device="cuda"),
+                                torch.tensor(np.asarray(q, np.float64), device="cuda"))
+    plan.close()
+    return E, F.cpu().numpy(), M
+
+
+def rel_rms(a, b):
+    return float(math.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
+
+
+def accuracy(se, torch, x, q, w, prec, F):
+    Eref, Fref, Mref = reference_forces(se, torch, x, q, w)
+    err = rel_rms(F.double().cpu().numpy(), Fref)
+    return {"rel_rms_force_err": err, "target": w["target_rel_force_err"],
+            "target_met": err <= w["target_rel_force_err"],
+            "reference": "FP64 SE on the GPU, P=24, M=%d" % Mref}
+
+
+def at_target(se, torch, x, q, w, prec, K, flush):
+    """Same workload at the smallest even P that meets the stated force error."""
+    N = len(q)
+    Eref, Fref, _ = reference_forces(se, torch, x, q, w)
+    for P in (8, 10, 12):
+        plan = se.Plan(N, w["L"], w["xi"], w["M"], P, precision=prec)
+        dt = plan.dtype
+        xd = torch.tensor(x, dtype=dt, device="cuda")
+        qd = torch.tensor(q, dtype=dt, device="cuda")
+        F = torch.empty((N, 3), dtype=dt, device="cuda")
+        phi = torch.empty((N,), dtype=dt, device="cuda")
+        for _ in range(10):
+            plan.evaluate(xd, qd, F, phi)
+        torch.cuda.synchronize()
+        err = rel_rms(F.double().cpu().numpy(), Fref)
+        if err > w["target_rel_force_err"]:
+            plan.close()
+            continue
+        k = max(50, min(K, 2000))
+        st = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        en = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        for i in range(k):
+            flush.zero_()
+            st[i].record()
+            plan.evaluate(xd, qd, F, phi)
+            en[i].record()
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in zip(st, en)) / k
+        plan.close()
+        return {"P": P, "value": 1e3 / ms, "unit": "evals/s", "ms_per_step": ms,
+                "ns_per_atom": ms * 1e6 / N, "rel_rms_force_err": err, "steps": k}
+    return None
+
+
+def e2e(se, torch, x, q, w, prec, K):
+    """Host buffers through se_energy_force_host: H2D of xyz and q, the
+    evaluation, D2H of F, phi and E, every step."""
+    N = len(q)
+    plan = se.Plan(N, w["L"], w["xi"], w["M"], w["P"], precision=prec)
+    dt = plan.dtype
+    hx = torch.tensor(x, dtype=dt).pin_memory()
+    hq = torch.tensor(q, dtype=dt).pin_memory()
+    hF = torch.empty((N, 3), dtype=dt).pin_memory()
+    hphi = torch.empty((N,), dtype=dt).pin_memory()
+    args = (hx.data_ptr(), hq.data_ptr(), hF.data_ptr(), hphi.data_ptr())
+    for _ in range(5):
+        plan.energy_force_host_ptrs(*args)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        plan.energy_force_host_ptrs(*args)
+    t1 = time.perf_counter()
+    plan.close()
+    es = hx.element_size()
+    return {"value": K / (t1 - t0), "unit": "evals/s", "steps": K,
+            "h2d_bytes_per_step": N * 4 * es, "d2h_bytes_per_step": N * 4 * es + 8 + 32,
+            "timing": "host wall clock around each synchronous call"}
+
+
+def cpu_baseline(x, q, w, seconds):
+    """The FP64 CPU oracle (plain SE, O2) on the host cores: whole evaluations of
+    the same workload, repeated for about `seconds`."""
+    import oracle
+    xd, qd = np.asarray(x, np.float64), np.asarray(q, np.float64)
+    cm = 64 if w["prec"] == "fp64" else 32
+    n, t0 = 0, time.perf_counter()
+    while True:
+        oracle.se_kspace(xd, qd, w["L"], w["xi"], w["M"], w["P"], cell_mode=cm)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (n >= 3 and el * (n + 1) / n > 3 * seconds):
+            break
+    return {"value": n / el, "unit": "evals/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d whole evaluations of %s by the FP64 CPU SE oracle (direct exp, direct "
+                      "DFT), %.1f s" % (n, "the workload", el)}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle (plain SE) on the host cores."""
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    x, q, w, prec = workload(args.workload)
+    xd, qd = np.asarray(x, np.float64), np.asarray(q, np.float64)
+    cm = 64 if w["prec"] == "fp64" else 32
+    t0 = time.perf_counter()
+    oracle.se_kspace(xd, qd, w["L"], w["xi"], w["M"], w["P"], cell_mode=cm)
+    t1 = time.perf_counter()
+    one = t1 - t0
+    budget = 150.0
+    W = args.warmup if one * (args.warmup + args.steps) <= budget else min(args.warmup, 1)
+    for _ in range(max(0, W - 1)):
+        oracle.se_kspace(xd, qd, w["L"], w["xi"], w["M"], w["P"], cell_mode=cm)
+    K = args.steps
+    run = K if one * K <= budget else max(1, int(budget / one))
+    t0 = time.perf_counter()
+    for _ in range(run):
+        oracle.se_kspace(xd, qd, w["L"], w["xi"], w["M"], w["P"], cell_mode=cm)
+    el = time.perf_counter() - t0
+    value = run / el
+    N = len(q)
+    sample = ("%d whole evaluations of the workload (of %d requested steps) by the FP64 CPU SE "
+              "oracle" % (run, K))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s",
+        "n_gpus": ws, "steps": K, "warmup": args.warmup, "ms_per_step": el / run * 1e3,
+        "ns_per_atom": el / run * 1e9 / N, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "N": N, "L": w["L"], "xi": w["xi"], "M": w["M"],
+                   "P": w["P"], "precision": w["prec"]},
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,170 @@
+/*
+ * se.h -- C ABI of libse, the Spectral Ewald (SE) k-space library for
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Method: D. Saffar Shamshirgar, B. Hess, A.-K. Tornberg, "A comparison of
+ * the Spectral Ewald and Smooth Particle Mesh Ewald methods in GROMACS",
+ * arXiv:1712.04718.  Section numbers below refer to that paper.
+ *
+ * Problem (Sec. 1, Eq. 1.1-1.3): N charges q_n at x_n in the periodic box
+ * [0, L)^3.  The library computes the Fourier-space (long-range) part of the
+ * Ewald sum (superscript L in Eq. 1.5-1.7) with the SE method of Sec. 3,
+ * i.e. the five steps of Algorithm 1 with the SE formulas of Table 2:
+ *   spread (Eq. 3.5) -> 3-D FFT -> scale (Eq. 3.6) -> inverse FFT ->
+ *   gather of potential (Eq. 3.9) and force (Sec. 3.1, Eq. 3.13).
+ * Results: phi^L_m, E^L = 1/2 sum q_m phi^L_m and F^L_m = -dE^L/dx_m.  The
+ * real-space and self terms of the Ewald sum are not included.  Units are
+ * the paper's Gaussian units (phi = sum q / r) times the prefactor set with
+ * se_plan_set_prefactor (default 1; 138.935458 gives kJ mol^-1 with nm and e).
+ *
+ * Parameters (Sec. 3 and Eq. 4.2): grid M^3, spacing h = L/M, support of P
+ * grid points per dimension (P even, 2..32, P <= M), half width w = P h / 2,
+ * shape m = c sqrt(pi P) with c = 0.95 by default, eta = (2 w xi / m)^2 =
+ * P L^2 xi^2 / (c^2 pi M^2), Gaussian exponent alpha = 2 xi^2 / eta.  For
+ * even P a particle in cell i = floor(x/h) (per dimension) covers grid
+ * points i - P/2 + 1 .. i + P/2 (the tensor-product box).
+ *
+ * Conventions for every call:
+ *  - Positions xyz are [N][3] (x, y, z interleaved), charges q are [N],
+ *    forces F are [N][3] and potentials phi are [N], all in the plan's
+ *    floating type (double for SE_FP64, float for SE_FP32).  Unless a
+ *    function says "host", pointers are DEVICE pointers on the plan's device.
+ *  - The caller owns every array it passes; outputs are overwritten, not
+ *    accumulated.  The plan owns its grids, tables, sort buffers and FFT
+ *    plans.
+ *  - Positions outside [0, L) are wrapped periodically.
+ *  - Calls are asynchronous on the plan's stream unless they return a host
+ *    value.  A plan must not be used by two host threads at once.
+ *  - Return value: SE_OK (0), a positive warning, or a negative error.  An
+ *    error leaves the outputs unspecified and the plan usable.
+ */
+#ifndef SE_H
+#define SE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SE_OK 0
+#define SE_WARN_NONNEUTRAL 1   /* |sum q| > 1e-10 sum |q|; the k = 0 mode is still dropped,
+                                  which equals a uniform neutralising background */
+#define SE_ERR_ARG (-1)        /* invalid argument (see each call) */
+#define SE_ERR_CUDA (-2)       /* a CUDA runtime call or kernel launch failed */
+#define SE_ERR_NOMEM (-3)      /* device or host allocation failed */
+#define SE_ERR_UNSUPPORTED (-4)/* valid but not supported: odd P, P > 32 */
+#define SE_ERR_CUFFT (-5)      /* a cuFFT call failed */
+#define SE_ERR_NONFINITE (-6)  /* a position or charge was NaN or infinite */
+
+/* precision modes */
+#define SE_FP64 0   /* every step in double precision */
+#define SE_FP32 1   /* single precision with compensated (two-sum) grid
+                       accumulation; Green's function table, grid energy and
+                       the final energy reduction in double precision */
+
+typedef struct se_plan se_plan;
+
+/* Create a plan for N particles in the box [0, L)^3 with Ewald parameter xi,
+ * grid M^3 and support P (Sec. 3; Eq. 4.2 fixes eta from c = 0.95).
+ * N >= 0 (N = 0 gives zero results), L > 0, xi > 0, 2 <= P <= min(M, 32),
+ * P even; otherwise SE_ERR_ARG (SE_ERR_UNSUPPORTED for odd P or P > 32).
+ * Device memory is allocated on the current CUDA device at the first
+ * computing call.  *out is set to NULL on failure. */
+int se_plan_create(se_plan **out, int64_t N, double L, double xi, int M, int P);
+
+/* Release every resource of the plan (NULL is accepted). */
+int se_plan_destroy(se_plan *plan);
+
+/* SE_FP64 (default) or SE_FP32. */
+int se_plan_set_precision(se_plan *plan, int prec);
+
+/* Shape of the Gaussian (Eq. 4.2): is_eta = 0 sets c (default 0.95), 1 sets
+ * eta directly; 0 < eta < 1 and c > 0 required. */
+int se_plan_set_shape(se_plan *plan, double value, int is_eta);
+
+/* Multiply phi, E and F by kc (default 1, Gaussian units; Sec. 4 remark:
+ * 1/(4 pi eps0) = 138.935458 kJ mol^-1 nm e^-2). */
+int se_plan_set_prefactor(se_plan *plan, double kc);
+
+/* CUDA stream (cudaStream_t) for every later call; NULL = legacy default. */
+int se_plan_set_stream(se_plan *plan, void *stream);
+
+/* Kernel tuning: spread_variant 0 = automatic, 1 = shared-memory tiles,
+ * 2 = direct global accumulation (FP64 only); tile = edge of a spreading tile
+ * in grid cells (0 = automatic, else 2..32).  For benchmarking and tests. */
+int se_plan_set_tuning(se_plan *plan, int spread_variant, int tile);
+
+/* Derived parameters: out[0..9] = h, w, eta, alpha, c_g, m, tile edge,
+ * spread variant in use (1 or 2), precision, prefactor.
+ * c_g = (2 xi^2 / (pi eta))^{3/2} is the Gaussian's normalisation (Eq. 3.5). */
+int se_plan_get_params(const se_plan *plan, double *out);
+
+/* Step (a) of Algorithm 1 with the SE window (Eq. 3.5): sort particles into
+ * grid tiles and spread H_j = sum_n q_n c_g exp(-alpha |x_j - x_n|^2) onto
+ * the plan's real grid (M^3, z fastest).  xyz, q: device. */
+int se_spread(se_plan *plan, const void *xyz, const void *q);
+
+/* Steps 3-5 of Algorithm 1: forward FFT of the spread grid, scaling by
+ * G(k)/M^3 with G(k) = 4 pi exp(-(1-eta) k^2 / (4 xi^2)) / k^2, G(0) = 0
+ * (Eq. 3.6 and the 4 pi of Eq. 3.7), inverse FFT into the gather grid.
+ * E_grid (device pointer to one double, or NULL) receives the grid energy
+ * kc h^3 / (2 M^3) sum_k G(k) |H^_k|^2, which equals E^L of the gather step
+ * to rounding.  Requires a preceding se_spread on this plan. */
+int se_scale(se_plan *plan, double *E_grid);
+
+/* Step 6 of Algorithm 1 (Eq. 3.9 and the analytic force of Sec. 3.1):
+ *   phi_m = kc h^3 sum_j Ht_j c_g exp(-alpha |x_j - x_m|^2)
+ *   F_m   = -kc 2 alpha h^3 q_m sum_j (x_j - x_m) Ht_j c_g exp(-alpha |x_j - x_m|^2)
+ * F_m is -dE/dx_m of the discrete SE energy.  Requires se_spread (with the
+ * same xyz, q) and se_scale.  phi, F and E (device pointer to one double,
+ * E = 1/2 sum q phi) may each be NULL. */
+int se_gather(se_plan *plan, const void *xyz, const void *q, void *phi, void *F,
+              double *E);
+
+/* The whole k-space evaluation: se_spread, se_scale, se_gather.  E is a HOST
+ * pointer (the call waits for the stream); F and phi are device pointers and
+ * may be NULL.  Returns SE_WARN_NONNEUTRAL for a non-neutral system and
+ * SE_ERR_NONFINITE for NaN/Inf input. */
+int se_energy_force(se_plan *plan, const void *xyz, const void *q, double *E,
+                    void *F, void *phi);
+
+/* As se_energy_force but every array is in HOST memory: the call copies xyz
+ * and q to the device, evaluates, and copies F, phi and E back before it
+ * returns.  Host arrays in page-locked memory make the copies asynchronous
+ * with respect to other host work. */
+int se_energy_force_host(se_plan *plan, const void *xyz, const void *q,
+                         double *E, void *F, void *phi);
+
+/* Copy one of the plan's grids into dst (device, M^3 values of the plan's
+ * type, z fastest): which = 0 spread grid H (after se_spread), 1 scaled and
+ * back-transformed grid Ht (after se_scale).  For tests and inspection. */
+int se_copy_grid(se_plan *plan, int which, void *dst);
+
+/* Self-energy term of Eq. 1.6, -kc xi / sqrt(pi) sum q^2, from HOST charges
+ * (double). Not part of the k-space result; provided for completeness. */
+int se_self_energy(const se_plan *plan, const double *q_host, int64_t n, double *E_self);
+
+/* Static message for a status code. */
+const char *se_strerror(int status);
+
+/* Stage timing (tracing).  enable = 1 records a CUDA event before and after
+ * every stage of each later evaluation on the plan's stream: 0 bin, 1
+ * scatter, 2 spread, 3 forward FFT, 4 scale, 5 inverse FFT, 6 gather.
+ * Events are recycled from a ring of 64 evaluations; completed ones are
+ * folded into running sums.  enable = 0 stops recording (sums are kept). */
+int se_plan_set_timing(se_plan *plan, int enable);
+
+/* Wait for recorded evaluations, then write the summed milliseconds of each
+ * stage to ms[0..6] (nstages >= 7) and the number of evaluations summed to
+ * *count; reset = 1 clears the sums afterwards. */
+int se_plan_get_timing(se_plan *plan, double *ms, int nstages, int64_t *count, int reset);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int se_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SE_H */

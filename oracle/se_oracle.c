@@ -34,8 +34,10 @@
  *  - Support: for even P the P points per dimension are
  *    i0 .. i0+P-1 with i0 = floor(x/h) - P/2 + 1 (tensor-product box).
  *  - eta = P L^2 xi^2 / (c^2 pi M^2) with c = 0.95 unless given (Eq. 4.2).
- *  - Positions are wrapped into [0, L) with x - L floor(x/L); a result that
- *    rounds to L is set to 0.  The cell index is floor(x/h), clamped to M-1.
+ *  - Positions inside [0, L) are used as given; others are wrapped with
+ *    x - L floor(x/L) (reciprocal of L rounded once), corrected once by L, and
+ *    set to 0 if still outside.  The cell index is floor(x M/L) (M/L rounded
+ *    once), clamped to M-1.
  *    When the oracle is compared with a single-precision GPU path, the
  *    wrap and the cell index are decided in single precision with the same
  *    operations as there (cell_mode = 32); all arithmetic after that integer
@@ -76,11 +78,20 @@ void oracle_set_num_threads(int n)
 /* Periodic wrap and cell index (reading: see header).                       */
 /* ------------------------------------------------------------------------ */
 
-static double wrap64(double x, double L)
+/* Double-precision wrap: untouched inside [0, L); otherwise x - L floor(x/L)
+ * with the reciprocal 1/L rounded once, each operation rounded (this file is
+ * compiled with -ffp-contract=off), then one correction by L either way;
+ * anything still outside becomes 0. */
+static double wrap64(double x, double L, double invL)
 {
-    double w = x - L * floor(x / L);
-    if (w >= L) w = 0.0;
-    if (w < 0.0) w = 0.0;
+    if (x >= 0.0 && x < L) return x;
+    double s = x * invL;
+    double f = floor(s);
+    double p = f * L;
+    double w = x - p;
+    if (w >= L) w = w - L;
+    if (w < 0.0) w = w + L;
+    if (!(w >= 0.0 && w < L)) w = 0.0;
     return w;
 }
 
@@ -96,7 +107,7 @@ static float wrap32(float x, float L, float invL)
     float w = x - p;
     if (w >= L) w = w - L;
     if (w < 0.0f) w = w + L;
-    if (w >= L || w < 0.0f) w = 0.0f;
+    if (!(w >= 0.0f && w < L)) w = 0.0f;
     return w;
 }
 
@@ -114,7 +125,7 @@ static void wrap_and_cell(double x, double L, int M, int cell_mode,
         c = (int)floorf(s);
         *xw = (double)wf;
     } else {
-        double w = wrap64(x, L);
+        double w = wrap64(x, L, 1.0 / L);
         double invh = (double)M / L;
         c = (int)floor(w * invh);
         *xw = w;

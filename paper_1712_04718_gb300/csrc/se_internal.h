@@ -1,0 +1,76 @@
+// se_internal.h -- types shared by the libse host code and its kernels.
+// Not part of the public ABI (see include/se.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace se {
+
+constexpr int kMaxP = 32;
+
+// A particle as (x, y, z, q), one 16- or 32-byte load.
+struct __align__(16) f4 { float x, y, z, w; };
+struct __align__(32) d4 { double x, y, z, w; };
+template <typename T> struct V4;
+template <> struct V4<float> { using type = f4; };
+template <> struct V4<double> { using type = d4; };
+template <typename T> using v4_t = typename V4<T>::type;
+
+// Per-evaluation constants passed by value to every kernel.
+template <typename T>
+struct KParams {
+    int N;          // particles
+    int M;          // grid points per dimension
+    int P;          // support points per dimension (even)
+    int tile;       // edge of a spreading tile, in grid cells
+    int nT;         // tiles per dimension = ceil(M / tile)
+    int ntiles;     // nT^3
+    T L, invL;      // box and its rounded reciprocal (wrap)
+    T h, invh;      // grid spacing and M / L rounded (cell index)
+    T beta;         // alpha h^2, the Gaussian exponent in grid units (alpha = 2 xi^2 / eta)
+    T qcg;          // c_g, folded into the spread weights
+    T phi_scale;    // kc h^3 c_g
+    T F_scale;      // -kc 2 alpha h^4 c_g (offsets are in grid units)
+    T E3[kMaxP];    // exp(-beta (a - (P-1)/2)^2), a = 0..P-1 (fast Gaussian gridding)
+};
+
+// Device-side results of the reducing kernels; each field is overwritten by
+// the last block of the kernel that produces it.
+struct Acc {
+    double sum_q;        // sum of charges (bin)
+    double sum_absq;     // sum of |q| (bin)
+    double e_grid;       // sum_k w_k G |H^_k|^2 over the half spectrum (scale)
+    double e_gather;     // sum_m q_m phi_m, phi including the prefactor (gather)
+    unsigned int nonfinite;  // number of particles with NaN/Inf position or charge (bin)
+    unsigned int pad0;
+    double pad[2];
+};
+
+// launchers (se_kernels_*.cu)
+template <typename T>
+cudaError_t launch_bin(const T* xyz, const T* q, const KParams<T>& kp, int* tile_count,
+                       int* slot, int* tile_of, int* tile_start, double* partials,
+                       unsigned* ticket, Acc* acc, cudaStream_t s);
+template <typename T>
+cudaError_t launch_scatter(const T* xyz, const T* q, const KParams<T>& kp, const int* slot,
+                           const int* tile_of, const int* tile_start, v4_t<T>* sorted,
+                           int* perm, cudaStream_t s);
+template <typename T>
+cudaError_t launch_spread_tiled(const v4_t<T>* sorted, const int* tile_start, T* grid,
+                                const KParams<T>& kp, bool comp, cudaStream_t s);
+template <typename T>
+cudaError_t launch_spread_direct(const v4_t<T>* sorted, T* grid, const KParams<T>& kp,
+                                 cudaStream_t s);
+template <typename T>
+cudaError_t launch_scale(void* cgrid, const double* green, int M, T* zero_grid,
+                         double* partials, unsigned* ticket, Acc* acc, double e_scale,
+                         double* E_out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_gather(const v4_t<T>* sorted, const int* perm, const T* grid, T* phi,
+                          T* F, const KParams<T>& kp, double* partials, unsigned* ticket,
+                          Acc* acc, double e_scale, double* E_out, cudaStream_t s);
+
+constexpr int kMaxPartials = 1024;   // blocks of the reducing kernels
+constexpr size_t kSmemBudget = 200 * 1024;  // dynamic shared memory for a spreading tile
+
+}  // namespace se

@@ -1,0 +1,606 @@
+// se_plan.cu -- libse host side: plans, device buffers, cuFFT plans and the
+// C ABI declared in include/se.h.
+//
+// One evaluation (se_energy_force) enqueues, on the plan's stream:
+//   k_bin (tile of each particle, slots, checks, tile offsets)
+//   k_scatter (particles in tile order)
+//   k_spread_{tiled,direct} (Eq. 3.5)
+//   cuFFT R2C
+//   k_scale (Eq. 3.6, grid energy; clears the spread grid for the next call)
+//   cuFFT C2R
+//   k_gather (Eq. 3.9 and the analytic force; energy 1/2 sum q phi)
+// and nothing else: no allocation, no memset, no host synchronisation except
+// the final copy of the energy when the caller asks for it on the host.
+#include <cufft.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/se.h"
+#include "se_internal.h"
+
+using se::Acc;
+using se::KParams;
+
+struct se_plan {
+    // user parameters
+    int64_t N = 0;
+    double L = 0, xi = 0;
+    int M = 0, P = 0;
+    int prec = SE_FP64;
+    double c_shape = 0.95, eta_user = 0.0;
+    int eta_fixed = 0;
+    double kc = 1.0;
+    cudaStream_t stream = nullptr;
+    int tune_variant = 0, tune_tile = 0;
+
+    // derived (set by derive())
+    double h = 0, w = 0, eta = 0, alpha = 0, cg = 0, m = 0;
+    int tile = 0, nT = 0, ntiles = 0, variant = 0;
+
+    // device state (prepare())
+    bool ready = false;
+    int ready_prec = -1;
+    int device = -1;
+    void* grid_spread = nullptr;   // M^3 real: spread output, FFT input
+    void* grid_gather = nullptr;   // M^3 real: inverse FFT output, gather input
+    void* cgrid = nullptr;         // M x M x (M/2+1) complex
+    double* green = nullptr;       // G(k) on the half spectrum (FP64)
+    int* tile_count = nullptr;
+    int* tile_start = nullptr;
+    int* slot = nullptr;
+    int* tile_of = nullptr;
+    int* perm = nullptr;
+    void* sorted = nullptr;
+    double* partials = nullptr;    // 5 x kMaxPartials
+    unsigned* tickets = nullptr;   // bin, scale, gather
+    Acc* acc = nullptr;
+    double* dE = nullptr;          // device energy for se_energy_force
+    cufftHandle fwd = 0, inv = 0;
+    bool have_fft = false;
+    // staging buffers of se_energy_force_host
+    void* h_xyz = nullptr;
+    void* h_q = nullptr;
+    void* h_F = nullptr;
+    void* h_phi = nullptr;
+
+    bool spread_clean = false;     // the spread grid is known to be zero
+    bool have_spread = false, have_scale = false;
+
+    // stage timing: a ring of event sets, one set (8 events) per evaluation
+    static constexpr int kStages = 7, kRing = 64;
+    bool timing = false;
+    cudaEvent_t ev[kRing][kStages + 1] = {};
+    bool ev_pending[kRing] = {};
+    bool ev_created = false;
+    int ev_cur = -1;               // set used by the evaluation in flight
+    int ev_next = 0;
+    double stage_ms[kStages] = {};
+    int64_t stage_count = 0;
+};
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+int check_cuda(cudaError_t e) { return e == cudaSuccess ? SE_OK : SE_ERR_CUDA; }
+
+// ---- stage timing ----
+void fold_set(se_plan* p, int i) {
+    if (!p->ev_pending[i]) return;
+    cudaEventSynchronize(p->ev[i][se_plan::kStages]);
+    for (int s = 0; s < se_plan::kStages; ++s) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p->ev[i][s], p->ev[i][s + 1]) == cudaSuccess)
+            p->stage_ms[s] += ms;
+    }
+    p->stage_count += 1;
+    p->ev_pending[i] = false;
+}
+
+// Start an evaluation's event set (no-op unless timing is on).
+void timing_begin(se_plan* p) {
+    p->ev_cur = -1;
+    if (!p->timing || !p->ev_created) return;
+    int i = p->ev_next;
+    p->ev_next = (i + 1) % se_plan::kRing;
+    fold_set(p, i);
+    p->ev_cur = i;
+    cudaEventRecord(p->ev[i][0], p->stream);
+}
+
+// Mark the end of stage s (0-based) of the evaluation in flight.
+void timing_mark(se_plan* p, int s) {
+    if (p->ev_cur < 0) return;
+    cudaEventRecord(p->ev[p->ev_cur][s + 1], p->stream);
+    if (s + 1 == se_plan::kStages) {
+        p->ev_pending[p->ev_cur] = true;
+        p->ev_cur = -1;
+    }
+}
+
+#define SE_TRY(expr)                      \
+    do {                                  \
+        int _rc = (expr);                 \
+        if (_rc != SE_OK) return _rc;     \
+    } while (0)
+#define SE_CUDA(expr) SE_TRY(check_cuda(expr))
+#define SE_CUFFT(expr)                                   \
+    do {                                                 \
+        if ((expr) != CUFFT_SUCCESS) return SE_ERR_CUFFT; \
+    } while (0)
+
+size_t tsize(int prec) { return prec == SE_FP64 ? sizeof(double) : sizeof(float); }
+
+// Sec. 3 and Eq. 4.2: h = L/M, w = P h / 2, m = c sqrt(pi P),
+// eta = (2 w xi / m)^2, alpha = 2 xi^2 / eta, c_g = (2 xi^2 / (pi eta))^{3/2}.
+void derive(se_plan* p) {
+    p->h = p->L / p->M;
+    p->w = p->P * p->h / 2.0;
+    p->m = p->c_shape * sqrt(kPi * p->P);
+    p->eta = p->eta_fixed ? p->eta_user : (2.0 * p->w * p->xi / p->m) * (2.0 * p->w * p->xi / p->m);
+    p->alpha = 2.0 * p->xi * p->xi / p->eta;
+    p->cg = pow(2.0 * p->xi * p->xi / (kPi * p->eta), 1.5);
+    // spreading variant and tile edge
+    int variant = p->tune_variant;
+    if (variant == 0) variant = (p->prec == SE_FP64 && p->P > 12) ? 2 : 1;
+    if (p->prec != SE_FP64) variant = 1;  // the compensated sum needs the tiles
+    p->variant = variant;
+    int tile = p->tune_tile > 0 ? p->tune_tile : 8;
+    if (tile > p->M) tile = p->M;
+    p->tile = tile;
+    p->nT = (p->M + tile - 1) / tile;
+    p->ntiles = p->nT * p->nT * p->nT;
+}
+
+void release_device(se_plan* p) {
+    if (p->have_fft) {
+        cufftDestroy(p->fwd);
+        cufftDestroy(p->inv);
+        p->have_fft = false;
+    }
+    void* bufs[] = {p->grid_spread, p->grid_gather, p->cgrid, p->green, p->tile_count,
+                    p->tile_start, p->slot, p->tile_of, p->perm, p->sorted, p->partials,
+                    p->tickets, p->acc, p->dE, p->h_xyz, p->h_q, p->h_F, p->h_phi};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    p->grid_spread = p->grid_gather = p->cgrid = p->sorted = nullptr;
+    p->green = p->partials = p->dE = nullptr;
+    p->tile_count = p->tile_start = p->slot = p->tile_of = p->perm = nullptr;
+    p->tickets = nullptr;
+    p->acc = nullptr;
+    p->h_xyz = p->h_q = p->h_F = p->h_phi = nullptr;
+    p->ready = false;
+    p->ready_prec = -1;
+}
+
+int dalloc(void** ptr, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    return cudaMalloc(ptr, bytes) == cudaSuccess ? SE_OK : SE_ERR_NOMEM;
+}
+
+template <typename T>
+KParams<T> make_kparams(const se_plan* p) {
+    KParams<T> kp;
+    memset(&kp, 0, sizeof(kp));
+    kp.N = (int)p->N;
+    kp.M = p->M;
+    kp.P = p->P;
+    kp.tile = p->tile;
+    kp.nT = p->nT;
+    kp.ntiles = p->ntiles;
+    kp.L = (T)p->L;
+    kp.invL = (T)(1.0 / p->L);
+    kp.h = (T)p->h;
+    kp.invh = (T)((double)p->M / p->L);
+    const double beta = p->alpha * p->h * p->h;
+    kp.beta = (T)beta;
+    kp.qcg = (T)p->cg;
+    kp.phi_scale = (T)(p->kc * p->h * p->h * p->h * p->cg);
+    kp.F_scale = (T)(-p->kc * 2.0 * p->alpha * p->h * p->h * p->h * p->h * p->cg);
+    for (int a = 0; a < p->P; ++a) {
+        const double ac = a - 0.5 * (p->P - 1);
+        kp.E3[a] = (T)exp(-beta * ac * ac);
+    }
+    return kp;
+}
+
+// G(k) = 4 pi exp(-(1-eta) k^2 / (4 xi^2)) / k^2 on the half spectrum, G(0) = 0.
+std::vector<double> green_table(const se_plan* p) {
+    const int M = p->M, Mh = M / 2 + 1;
+    std::vector<double> g((size_t)M * M * Mh);
+    const double t = 2.0 * kPi / p->L;
+    for (int kx = 0; kx < M; ++kx) {
+        const int sx = (2 * kx <= M) ? kx : kx - M;
+        for (int ky = 0; ky < M; ++ky) {
+            const int sy = (2 * ky <= M) ? ky : ky - M;
+            for (int kz = 0; kz < Mh; ++kz) {
+                const double n2 = (double)sx * sx + (double)sy * sy + (double)kz * kz;
+                double v = 0.0;
+                if (n2 > 0) {
+                    const double k2 = t * t * n2;
+                    v = 4.0 * kPi * exp(-(1.0 - p->eta) * k2 / (4.0 * p->xi * p->xi)) / k2;
+                }
+                g[((size_t)kx * M + ky) * Mh + kz] = v;
+            }
+        }
+    }
+    return g;
+}
+
+int prepare(se_plan* p) {
+    int dev = 0;
+    SE_CUDA(cudaGetDevice(&dev));
+    if (p->ready && p->ready_prec == p->prec && p->device == dev) return SE_OK;
+    release_device(p);
+    derive(p);
+    p->device = dev;
+    const size_t ts = tsize(p->prec);
+    const size_t M3 = (size_t)p->M * p->M * p->M;
+    const size_t nc = (size_t)p->M * p->M * (p->M / 2 + 1);
+    const size_t N = (size_t)p->N;
+    int rc = SE_OK;
+    if (rc == SE_OK) rc = dalloc(&p->grid_spread, M3 * ts);
+    if (rc == SE_OK) rc = dalloc(&p->grid_gather, M3 * ts);
+    if (rc == SE_OK) rc = dalloc(&p->cgrid, nc * 2 * ts);
+    if (rc == SE_OK) rc = dalloc((void**)&p->green, nc * sizeof(double));
+    if (rc == SE_OK) rc = dalloc((void**)&p->tile_count, (size_t)p->ntiles * sizeof(int));
+    if (rc == SE_OK) rc = dalloc((void**)&p->tile_start, ((size_t)p->ntiles + 1) * sizeof(int));
+    if (rc == SE_OK) rc = dalloc((void**)&p->slot, N * sizeof(int));
+    if (rc == SE_OK) rc = dalloc((void**)&p->tile_of, N * sizeof(int));
+    if (rc == SE_OK) rc = dalloc((void**)&p->perm, N * sizeof(int));
+    if (rc == SE_OK) rc = dalloc(&p->sorted, N * 4 * ts);
+    if (rc == SE_OK) rc = dalloc((void**)&p->partials, 5 * se::kMaxPartials * sizeof(double));
+    if (rc == SE_OK) rc = dalloc((void**)&p->tickets, 4 * sizeof(unsigned));
+    if (rc == SE_OK) rc = dalloc((void**)&p->acc, sizeof(Acc));
+    if (rc == SE_OK) rc = dalloc((void**)&p->dE, sizeof(double));
+    if (rc != SE_OK) {
+        release_device(p);
+        return rc;
+    }
+    std::vector<double> g = green_table(p);
+    if (cudaMemcpy(p->green, g.data(), nc * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(p->tile_count, 0, (size_t)p->ntiles * sizeof(int)) != cudaSuccess ||
+        cudaMemset(p->tickets, 0, 4 * sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(p->acc, 0, sizeof(Acc)) != cudaSuccess ||
+        cudaMemset(p->grid_spread, 0, M3 * ts) != cudaSuccess) {
+        release_device(p);
+        return SE_ERR_CUDA;
+    }
+    const cufftType tf = p->prec == SE_FP64 ? CUFFT_D2Z : CUFFT_R2C;
+    const cufftType ti = p->prec == SE_FP64 ? CUFFT_Z2D : CUFFT_C2R;
+    if (cufftPlan3d(&p->fwd, p->M, p->M, p->M, tf) != CUFFT_SUCCESS) {
+        release_device(p);
+        return SE_ERR_CUFFT;
+    }
+    if (cufftPlan3d(&p->inv, p->M, p->M, p->M, ti) != CUFFT_SUCCESS) {
+        cufftDestroy(p->fwd);
+        release_device(p);
+        return SE_ERR_CUFFT;
+    }
+    p->have_fft = true;
+    p->spread_clean = true;
+    p->have_spread = p->have_scale = false;
+    p->ready = true;
+    p->ready_prec = p->prec;
+    return SE_OK;
+}
+
+void invalidate(se_plan* p) {
+    // parameters changed: rebuild tables and buffers at the next call
+    if (p->ready) release_device(p);
+    derive(p);
+}
+
+template <typename T>
+int do_spread(se_plan* p, const void* xyz, const void* q) {
+    const KParams<T> kp = make_kparams<T>(p);
+    using V = se::v4_t<T>;
+    const size_t M3 = (size_t)p->M * p->M * p->M;
+    if (!p->spread_clean) SE_CUDA(cudaMemsetAsync(p->grid_spread, 0, M3 * sizeof(T), p->stream));
+    timing_begin(p);
+    SE_CUDA(se::launch_bin<T>((const T*)xyz, (const T*)q, kp, p->tile_count, p->slot, p->tile_of,
+                              p->tile_start, p->partials, p->tickets + 0, p->acc, p->stream));
+    timing_mark(p, 0);
+    SE_CUDA(se::launch_scatter<T>((const T*)xyz, (const T*)q, kp, p->slot, p->tile_of,
+                                  p->tile_start, (V*)p->sorted, p->perm, p->stream));
+    timing_mark(p, 1);
+    if (p->N > 0) {
+        if (p->variant == 2)
+            SE_CUDA(se::launch_spread_direct<T>((const V*)p->sorted, (T*)p->grid_spread, kp, p->stream));
+        else
+            SE_CUDA(se::launch_spread_tiled<T>((const V*)p->sorted, p->tile_start, (T*)p->grid_spread,
+                                               kp, p->prec != SE_FP64, p->stream));
+    }
+    timing_mark(p, 2);
+    p->spread_clean = false;
+    p->have_spread = true;
+    p->have_scale = false;
+    return SE_OK;
+}
+
+template <typename T>
+int do_scale(se_plan* p, double* E_grid) {
+    SE_CUFFT(cufftSetStream(p->fwd, p->stream));
+    SE_CUFFT(cufftSetStream(p->inv, p->stream));
+    if (p->prec == SE_FP64)
+        SE_CUFFT(cufftExecD2Z(p->fwd, (cufftDoubleReal*)p->grid_spread, (cufftDoubleComplex*)p->cgrid));
+    else
+        SE_CUFFT(cufftExecR2C(p->fwd, (cufftReal*)p->grid_spread, (cufftComplex*)p->cgrid));
+    timing_mark(p, 3);
+    const double M3 = (double)p->M * p->M * p->M;
+    const double e_scale = p->kc * p->h * p->h * p->h / (2.0 * M3);
+    SE_CUDA(se::launch_scale<T>(p->cgrid, p->green, p->M, (T*)p->grid_spread, p->partials + 3 * se::kMaxPartials,
+                                p->tickets + 1, p->acc, e_scale, E_grid, p->stream));
+    timing_mark(p, 4);
+    p->spread_clean = true;
+    if (p->prec == SE_FP64)
+        SE_CUFFT(cufftExecZ2D(p->inv, (cufftDoubleComplex*)p->cgrid, (cufftDoubleReal*)p->grid_gather));
+    else
+        SE_CUFFT(cufftExecC2R(p->inv, (cufftComplex*)p->cgrid, (cufftReal*)p->grid_gather));
+    timing_mark(p, 5);
+    p->have_scale = true;
+    return SE_OK;
+}
+
+template <typename T>
+int do_gather(se_plan* p, void* phi, void* F, double* E) {
+    const KParams<T> kp = make_kparams<T>(p);
+    using V = se::v4_t<T>;
+    SE_CUDA(se::launch_gather<T>((const V*)p->sorted, p->perm, (const T*)p->grid_gather, (T*)phi,
+                                 (T*)F, kp, p->partials + 4 * se::kMaxPartials, p->tickets + 2,
+                                 p->acc, 0.5, E, p->stream));
+    timing_mark(p, 6);
+    return SE_OK;
+}
+
+int status_from_acc(const Acc& a) {
+    if (a.nonfinite) return SE_ERR_NONFINITE;
+    if (fabs(a.sum_q) > 1e-10 * a.sum_absq) return SE_WARN_NONNEUTRAL;
+    return SE_OK;
+}
+
+int evaluate(se_plan* p, const void* xyz, const void* q, void* F, void* phi, double* dE) {
+    if (p->prec == SE_FP64) {
+        SE_TRY(do_spread<double>(p, xyz, q));
+        SE_TRY(do_scale<double>(p, nullptr));
+        SE_TRY(do_gather<double>(p, phi, F, dE));
+    } else {
+        SE_TRY(do_spread<float>(p, xyz, q));
+        SE_TRY(do_scale<float>(p, nullptr));
+        SE_TRY(do_gather<float>(p, phi, F, dE));
+    }
+    return SE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int se_plan_create(se_plan** out, int64_t N, double L, double xi, int M, int P) {
+    if (!out) return SE_ERR_ARG;
+    *out = nullptr;
+    if (N < 0 || N > 0x7fffffffLL) return SE_ERR_ARG;
+    if (!(L > 0) || !isfinite(L) || !(xi > 0) || !isfinite(xi)) return SE_ERR_ARG;
+    if (M < 2 || P < 2 || P > M) return SE_ERR_ARG;
+    if ((P & 1) || P > se::kMaxP) return SE_ERR_UNSUPPORTED;
+    if ((double)M * M * M > 2.0e9) return SE_ERR_ARG;
+    se_plan* p = new (std::nothrow) se_plan();
+    if (!p) return SE_ERR_NOMEM;
+    p->N = N;
+    p->L = L;
+    p->xi = xi;
+    p->M = M;
+    p->P = P;
+    derive(p);
+    if (!(p->eta > 0.0 && p->eta < 1.0)) {
+        delete p;
+        return SE_ERR_ARG;
+    }
+    *out = p;
+    return SE_OK;
+}
+
+int se_plan_destroy(se_plan* p) {
+    if (!p) return SE_OK;
+    if (p->ev_created) {
+        for (int i = 0; i < se_plan::kRing; ++i)
+            for (int s = 0; s <= se_plan::kStages; ++s) cudaEventDestroy(p->ev[i][s]);
+        p->ev_created = false;
+    }
+    int cur = -1;
+    if (p->ready && cudaGetDevice(&cur) == cudaSuccess && cur != p->device) {
+        cudaSetDevice(p->device);
+        release_device(p);
+        cudaSetDevice(cur);
+    } else {
+        release_device(p);
+    }
+    delete p;
+    return SE_OK;
+}
+
+int se_plan_set_precision(se_plan* p, int prec) {
+    if (!p || (prec != SE_FP64 && prec != SE_FP32)) return SE_ERR_ARG;
+    if (prec != p->prec) {
+        p->prec = prec;
+        invalidate(p);
+    }
+    return SE_OK;
+}
+
+int se_plan_set_shape(se_plan* p, double value, int is_eta) {
+    if (!p || !isfinite(value)) return SE_ERR_ARG;
+    if (is_eta) {
+        if (!(value > 0.0 && value < 1.0)) return SE_ERR_ARG;
+        p->eta_fixed = 1;
+        p->eta_user = value;
+    } else {
+        if (!(value > 0.0)) return SE_ERR_ARG;
+        double m = value * sqrt(kPi * p->P);
+        double eta = (2.0 * p->w * p->xi / m) * (2.0 * p->w * p->xi / m);
+        if (!(eta > 0.0 && eta < 1.0)) return SE_ERR_ARG;
+        p->eta_fixed = 0;
+        p->c_shape = value;
+    }
+    invalidate(p);
+    return SE_OK;
+}
+
+int se_plan_set_prefactor(se_plan* p, double kc) {
+    if (!p || !isfinite(kc)) return SE_ERR_ARG;
+    p->kc = kc;  // only the kernel parameters change
+    return SE_OK;
+}
+
+int se_plan_set_stream(se_plan* p, void* stream) {
+    if (!p) return SE_ERR_ARG;
+    p->stream = (cudaStream_t)stream;
+    return SE_OK;
+}
+
+int se_plan_set_tuning(se_plan* p, int spread_variant, int tile) {
+    if (!p || spread_variant < 0 || spread_variant > 2 || (tile != 0 && (tile < 2 || tile > 32)))
+        return SE_ERR_ARG;
+    if (spread_variant == 2 && p->prec != SE_FP64) return SE_ERR_UNSUPPORTED;
+    p->tune_variant = spread_variant;
+    p->tune_tile = tile;
+    invalidate(p);
+    return SE_OK;
+}
+
+int se_plan_get_params(const se_plan* p, double* out) {
+    if (!p || !out) return SE_ERR_ARG;
+    out[0] = p->h;
+    out[1] = p->w;
+    out[2] = p->eta;
+    out[3] = p->alpha;
+    out[4] = p->cg;
+    out[5] = p->m;
+    out[6] = p->tile;
+    out[7] = p->variant;
+    out[8] = p->prec;
+    out[9] = p->kc;
+    return SE_OK;
+}
+
+int se_spread(se_plan* p, const void* xyz, const void* q) {
+    if (!p || (p->N > 0 && (!xyz || !q))) return SE_ERR_ARG;
+    SE_TRY(prepare(p));
+    return p->prec == SE_FP64 ? do_spread<double>(p, xyz, q) : do_spread<float>(p, xyz, q);
+}
+
+int se_scale(se_plan* p, double* E_grid) {
+    if (!p) return SE_ERR_ARG;
+    if (!p->ready || !p->have_spread) return SE_ERR_ARG;
+    return p->prec == SE_FP64 ? do_scale<double>(p, E_grid) : do_scale<float>(p, E_grid);
+}
+
+int se_gather(se_plan* p, const void* xyz, const void* q, void* phi, void* F, double* E) {
+    if (!p || (p->N > 0 && (!xyz || !q))) return SE_ERR_ARG;
+    if (!p->ready || !p->have_scale) return SE_ERR_ARG;
+    return p->prec == SE_FP64 ? do_gather<double>(p, phi, F, E) : do_gather<float>(p, phi, F, E);
+}
+
+int se_energy_force(se_plan* p, const void* xyz, const void* q, double* E, void* F, void* phi) {
+    if (!p || (p->N > 0 && (!xyz || !q))) return SE_ERR_ARG;
+    SE_TRY(prepare(p));
+    SE_TRY(evaluate(p, xyz, q, F, phi, p->dE));
+    if (E) {
+        Acc a;
+        SE_CUDA(cudaMemcpyAsync(&a, p->acc, sizeof(Acc), cudaMemcpyDeviceToHost, p->stream));
+        SE_CUDA(cudaStreamSynchronize(p->stream));
+        *E = 0.5 * a.e_gather;
+        return status_from_acc(a);
+    }
+    return SE_OK;
+}
+
+int se_energy_force_host(se_plan* p, const void* xyz, const void* q, double* E, void* F, void* phi) {
+    if (!p || (p->N > 0 && (!xyz || !q))) return SE_ERR_ARG;
+    SE_TRY(prepare(p));
+    const size_t ts = tsize(p->prec), N = (size_t)p->N;
+    if (!p->h_xyz) {
+        int rc = SE_OK;
+        if (rc == SE_OK) rc = dalloc(&p->h_xyz, 3 * N * ts);
+        if (rc == SE_OK) rc = dalloc(&p->h_q, N * ts);
+        if (rc == SE_OK) rc = dalloc(&p->h_F, 3 * N * ts);
+        if (rc == SE_OK) rc = dalloc(&p->h_phi, N * ts);
+        if (rc != SE_OK) return rc;
+    }
+    if (N > 0) {
+        SE_CUDA(cudaMemcpyAsync(p->h_xyz, xyz, 3 * N * ts, cudaMemcpyHostToDevice, p->stream));
+        SE_CUDA(cudaMemcpyAsync(p->h_q, q, N * ts, cudaMemcpyHostToDevice, p->stream));
+    }
+    SE_TRY(evaluate(p, p->h_xyz, p->h_q, F ? p->h_F : nullptr, phi ? p->h_phi : nullptr, p->dE));
+    if (N > 0 && F) SE_CUDA(cudaMemcpyAsync(F, p->h_F, 3 * N * ts, cudaMemcpyDeviceToHost, p->stream));
+    if (N > 0 && phi) SE_CUDA(cudaMemcpyAsync(phi, p->h_phi, N * ts, cudaMemcpyDeviceToHost, p->stream));
+    Acc a;
+    SE_CUDA(cudaMemcpyAsync(&a, p->acc, sizeof(Acc), cudaMemcpyDeviceToHost, p->stream));
+    SE_CUDA(cudaStreamSynchronize(p->stream));
+    if (E) *E = 0.5 * a.e_gather;
+    return status_from_acc(a);
+}
+
+int se_copy_grid(se_plan* p, int which, void* dst) {
+    if (!p || !dst || (which != 0 && which != 1)) return SE_ERR_ARG;
+    if (!p->ready) return SE_ERR_ARG;
+    const size_t bytes = (size_t)p->M * p->M * p->M * tsize(p->prec);
+    SE_CUDA(cudaMemcpyAsync(dst, which == 0 ? p->grid_spread : p->grid_gather, bytes,
+                            cudaMemcpyDeviceToDevice, p->stream));
+    return SE_OK;
+}
+
+int se_self_energy(const se_plan* p, const double* q_host, int64_t n, double* E_self) {
+    if (!p || !E_self || n < 0 || (n > 0 && !q_host)) return SE_ERR_ARG;
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += q_host[i] * q_host[i];
+    *E_self = -p->kc * p->xi / sqrt(kPi) * s;
+    return SE_OK;
+}
+
+const char* se_strerror(int status) {
+    switch (status) {
+        case SE_OK: return "success";
+        case SE_WARN_NONNEUTRAL: return "warning: the system is not charge neutral";
+        case SE_ERR_ARG: return "invalid argument";
+        case SE_ERR_CUDA: return "CUDA error";
+        case SE_ERR_NOMEM: return "out of memory";
+        case SE_ERR_UNSUPPORTED: return "unsupported parameter (odd P or P > 32)";
+        case SE_ERR_CUFFT: return "cuFFT error";
+        case SE_ERR_NONFINITE: return "non-finite position or charge";
+        default: return "unknown status";
+    }
+}
+
+int se_plan_set_timing(se_plan* p, int enable) {
+    if (!p) return SE_ERR_ARG;
+    if (enable && !p->ev_created) {
+        for (int i = 0; i < se_plan::kRing; ++i)
+            for (int s = 0; s <= se_plan::kStages; ++s)
+                SE_CUDA(cudaEventCreate(&p->ev[i][s]));
+        p->ev_created = true;
+    }
+    p->timing = enable != 0;
+    return SE_OK;
+}
+
+int se_plan_get_timing(se_plan* p, double* ms, int nstages, int64_t* count, int reset) {
+    if (!p || !ms || nstages < se_plan::kStages) return SE_ERR_ARG;
+    if (p->ev_created)
+        for (int i = 0; i < se_plan::kRing; ++i) fold_set(p, i);
+    for (int s = 0; s < se_plan::kStages; ++s) ms[s] = p->stage_ms[s];
+    if (count) *count = p->stage_count;
+    if (reset) {
+        for (int s = 0; s < se_plan::kStages; ++s) p->stage_ms[s] = 0.0;
+        p->stage_count = 0;
+    }
+    return SE_OK;
+}
+
+int se_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,215 @@
+"""Python front end of libse: a plan object over the C ABI of include/se.h.
+
+PyTorch supplies device memory and streams; every step of the computation
+runs in libse's CUDA kernels (and cuFFT).  Each call is issued on torch's
+current CUDA stream, so it is ordered with surrounding torch work.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _native as nat
+
+PRECISIONS = {"fp64": nat.SE_FP64, "fp32": nat.SE_FP32}
+_TORCH_DTYPE = {nat.SE_FP64: torch.float64, nat.SE_FP32: torch.float32}
+_NP_DTYPE = {nat.SE_FP64: np.float64, nat.SE_FP32: np.float32}
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Plan:
+    """SE k-space plan for N particles in [0, L)^3 (xi, grid M^3, support P).
+
+    precision: "fp64" (every step in double) or "fp32" (single precision with
+    compensated grid sums; FP64 Green's function table and energy reduction).
+    """
+
+    def __init__(self, N, L, xi, M, P, precision="fp64", c=None, eta=None,
+                 prefactor=None, spread_variant=0, tile=0):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libse needs a CUDA device; none is available")
+        self._lib = nat.load()
+        self._h = ctypes.c_void_p()
+        nat.check(self._lib.se_plan_create(ctypes.byref(self._h), int(N), float(L),
+                                           float(xi), int(M), int(P)), "se_plan_create")
+        self.N, self.L, self.xi, self.M, self.P = int(N), float(L), float(xi), int(M), int(P)
+        self.prec = PRECISIONS[precision]
+        nat.check(self._lib.se_plan_set_precision(self._h, self.prec), "se_plan_set_precision")
+        if c is not None:
+            nat.check(self._lib.se_plan_set_shape(self._h, float(c), 0), "se_plan_set_shape")
+        if eta is not None:
+            nat.check(self._lib.se_plan_set_shape(self._h, float(eta), 1), "se_plan_set_shape")
+        if prefactor is not None:
+            nat.check(self._lib.se_plan_set_prefactor(self._h, float(prefactor)),
+                      "se_plan_set_prefactor")
+        if spread_variant or tile:
+            nat.check(self._lib.se_plan_set_tuning(self._h, int(spread_variant), int(tile)),
+                      "se_plan_set_tuning")
+        self.last_status = 0
+
+    # -- bookkeeping -------------------------------------------------------
+    @property
+    def dtype(self):
+        return _TORCH_DTYPE[self.prec]
+
+    @property
+    def np_dtype(self):
+        return _NP_DTYPE[self.prec]
+
+    def params(self):
+        out = (ctypes.c_double * 10)()
+        nat.check(self._lib.se_plan_get_params(self._h, out), "se_plan_get_params")
+        keys = ["h", "w", "eta", "alpha", "cg", "m", "tile", "spread_variant", "precision",
+                "prefactor"]
+        return dict(zip(keys, list(out)))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.se_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self):
+        s = torch.cuda.current_stream().cuda_stream
+        nat.check(self._lib.se_plan_set_stream(self._h, ctypes.c_void_p(s)), "se_plan_set_stream")
+
+    def _check_inputs(self, xyz, q):
+        if xyz.dtype != self.dtype or q.dtype != self.dtype:
+            raise TypeError("xyz and q must be %s" % self.dtype)
+        if not (xyz.is_cuda and q.is_cuda):
+            raise TypeError("xyz and q must be CUDA tensors")
+        if tuple(xyz.shape) != (self.N, 3) or tuple(q.shape) != (self.N,):
+            raise ValueError("expected xyz [%d, 3] and q [%d]" % (self.N, self.N))
+        if not (xyz.is_contiguous() and q.is_contiguous()):
+            raise ValueError("xyz and q must be contiguous")
+
+    # -- the five steps ----------------------------------------------------
+    def spread(self, xyz, q):
+        self._check_inputs(xyz, q)
+        self._stream()
+        nat.check(self._lib.se_spread(self._h, _ptr(xyz), _ptr(q)), "se_spread")
+
+    def scale(self, E_grid=None):
+        """FFT, Green's-function scaling, inverse FFT.  E_grid: optional CUDA
+        float64 tensor of one element receiving the grid energy."""
+        self._stream()
+        nat.check(self._lib.se_scale(self._h, _ptr(E_grid)), "se_scale")
+
+    def gather(self, xyz, q, phi=None, F=None, E=None):
+        self._check_inputs(xyz, q)
+        self._stream()
+        nat.check(self._lib.se_gather(self._h, _ptr(xyz), _ptr(q), _ptr(phi), _ptr(F), _ptr(E)),
+                  "se_gather")
+
+    def energy_force(self, xyz, q, with_phi=True, F=None, phi=None):
+        """E (python float), F [N,3], phi [N] (CUDA tensors of the plan's dtype)."""
+        self._check_inputs(xyz, q)
+        if F is None:
+            F = torch.empty((self.N, 3), dtype=self.dtype, device=xyz.device)
+        if phi is None and with_phi:
+            phi = torch.empty((self.N,), dtype=self.dtype, device=xyz.device)
+        self._stream()
+        E = ctypes.c_double()
+        st = self._lib.se_energy_force(self._h, _ptr(xyz), _ptr(q), ctypes.byref(E), _ptr(F),
+                                       _ptr(phi))
+        self.last_status = nat.check(st, "se_energy_force")
+        return E.value, F, phi
+
+    def energy_force_host(self, xyz, q):
+        """Host (numpy) in, host out: copies to the device, evaluates, copies back."""
+        xyz = np.ascontiguousarray(xyz, dtype=self.np_dtype)
+        q = np.ascontiguousarray(q, dtype=self.np_dtype)
+        F = np.empty((self.N, 3), dtype=self.np_dtype)
+        phi = np.empty((self.N,), dtype=self.np_dtype)
+        self._stream()
+        E = ctypes.c_double()
+        st = self._lib.se_energy_force_host(
+            self._h, xyz.ctypes.data_as(ctypes.c_void_p), q.ctypes.data_as(ctypes.c_void_p),
+            ctypes.byref(E), F.ctypes.data_as(ctypes.c_void_p),
+            phi.ctypes.data_as(ctypes.c_void_p))
+        self.last_status = nat.check(st, "se_energy_force_host")
+        return E.value, F, phi
+
+    def energy_force_host_ptrs(self, xyz_ptr, q_ptr, F_ptr, phi_ptr):
+        """se_energy_force_host on raw host pointers (e.g. pinned torch tensors)."""
+        self._stream()
+        E = ctypes.c_double()
+        st = self._lib.se_energy_force_host(self._h, ctypes.c_void_p(xyz_ptr),
+                                            ctypes.c_void_p(q_ptr), ctypes.byref(E),
+                                            ctypes.c_void_p(F_ptr), ctypes.c_void_p(phi_ptr))
+        self.last_status = nat.check(st, "se_energy_force_host")
+        return E.value
+
+    STAGES = ("bin", "scatter", "spread", "fft_fwd", "scale", "fft_inv", "gather")
+
+    def set_timing(self, enable=True):
+        nat.check(self._lib.se_plan_set_timing(self._h, int(bool(enable))), "se_plan_set_timing")
+
+    def get_timing(self, reset=True):
+        """(summed ms per stage as a dict, number of evaluations summed)."""
+        ms = (ctypes.c_double * 7)()
+        n = ctypes.c_int64()
+        nat.check(self._lib.se_plan_get_timing(self._h, ms, 7, ctypes.byref(n), int(reset)),
+                  "se_plan_get_timing")
+        return dict(zip(self.STAGES, list(ms))), n.value
+
+    def evaluate(self, xyz, q, F, phi=None, E=None):
+        """spread + scale + gather without any host synchronisation (E: optional
+        CUDA float64 tensor of one element)."""
+        self._stream()
+        h = self._h
+        chk = nat.check
+        chk(self._lib.se_spread(h, _ptr(xyz), _ptr(q)), "se_spread")
+        chk(self._lib.se_scale(h, None), "se_scale")
+        chk(self._lib.se_gather(h, _ptr(xyz), _ptr(q), _ptr(phi), _ptr(F), _ptr(E)), "se_gather")
+
+    def copy_grid(self, which):
+        """0: spread grid H (valid after spread), 1: Ht (after scale); [M,M,M] tensor."""
+        out = torch.empty((self.M, self.M, self.M), dtype=self.dtype, device="cuda")
+        self._stream()
+        nat.check(self._lib.se_copy_grid(self._h, int(which), _ptr(out)), "se_copy_grid")
+        return out
+
+    def self_energy(self, q):
+        q = np.ascontiguousarray(np.asarray(q, dtype=np.float64))
+        E = ctypes.c_double()
+        nat.check(self._lib.se_self_energy(self._h, q.ctypes.data_as(ctypes.c_void_p), len(q),
+                                           ctypes.byref(E)), "se_self_energy")
+        return E.value
+
+
+# C-ABI names, for callers who want the flat interface.
+def se_plan_create(N, L, xi, M, P, **kw):
+    return Plan(N, L, xi, M, P, **kw)
+
+
+def se_spread(plan, xyz, q):
+    return plan.spread(xyz, q)
+
+
+def se_scale(plan, E_grid=None):
+    return plan.scale(E_grid)
+
+
+def se_gather(plan, xyz, q, phi=None, F=None, E=None):
+    return plan.gather(xyz, q, phi, F, E)
+
+
+def se_energy_force(plan, xyz, q, **kw):
+    return plan.energy_force(xyz, q, **kw)
+
+
+def se_energy_force_host(plan, xyz, q):
+    return plan.energy_force_host(xyz, q)
+
+
+def se_plan_destroy(plan):
+    plan.close()

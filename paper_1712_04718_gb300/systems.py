@@ -1,6 +1,6 @@
 """Seeded synthetic particle systems (inputs only; no Ewald/SE arithmetic).
 
-This module is shared by the tests, the oracle checks and the benchmark.  It
+This module is shared by the tests and the benchmark.  It
 draws positions and charges and holds the named workload parameters; it
 computes nothing of the method itself.
 

@@ -1,0 +1,289 @@
+"""GPU parity: libse (through its C ABI) against the FP64 CPU oracle.
+
+Tolerances (derived from the arithmetic):
+* FP64 path vs O2 (the same discrete SE quantity): rounding only, 1e-12
+  relative (normwise over all particles or grid points).
+* FP32 path vs O2: single-precision spread/FFT/gather with ~1e-7 rounding per
+  operation, a few hundred operations deep in the FFT and the P^3 sums:
+  2e-5 relative normwise; the integer decisions (wrap, cell) are taken in
+  float32 on both sides (oracle cell_mode=32).
+* vs O1 (the exact Ewald k-space sum): each workload's stated relative rms
+  force error.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1712_04718_gb300 import _native as nat
+from paper_1712_04718_gb300 import se, systems
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 2e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    d = math.sqrt(((a - b) ** 2).sum())
+    n = math.sqrt((b ** 2).sum())
+    return d / n if n > 0 else d
+
+
+def run_gpu(x, q, L, xi, M, P, prec, grids=False, **kw):
+    plan = se.Plan(len(q), L, xi, M, P, precision=prec, **kw)
+    dt = plan.dtype
+    xd = torch.as_tensor(np.asarray(x), dtype=dt).cuda().contiguous()
+    qd = torch.as_tensor(np.asarray(q), dtype=dt).cuda().contiguous()
+    out = {}
+    if grids:
+        plan.spread(xd, qd)
+        out["H"] = plan.copy_grid(0).double().cpu().numpy()
+        Eg = torch.zeros(1, dtype=torch.float64, device="cuda")
+        plan.scale(Eg)
+        out["Ht"] = plan.copy_grid(1).double().cpu().numpy()
+        phi = torch.empty(len(q), dtype=dt, device="cuda")
+        F = torch.empty((len(q), 3), dtype=dt, device="cuda")
+        E = torch.zeros(1, dtype=torch.float64, device="cuda")
+        plan.gather(xd, qd, phi, F, E)
+        torch.cuda.synchronize()
+        out.update(E=E.item(), E_grid=Eg.item(), F=F.double().cpu().numpy(),
+                   phi=phi.double().cpu().numpy())
+    else:
+        E, F, phi = plan.energy_force(xd, qd)
+        out.update(E=E, F=F.double().cpu().numpy(), phi=phi.double().cpu().numpy(),
+                   status=plan.last_status)
+    out["params"] = plan.params()
+    out["xd"] = xd
+    plan.close()
+    return out
+
+
+def oracle_for(x, q, L, xi, M, P, prec, grids=False):
+    cm = 32 if prec == "fp32" else 64
+    return oracle.se_kspace(np.asarray(x, dtype=np.float64), np.asarray(q, dtype=np.float64),
+                            L, xi, M, P, cell_mode=cm, grids=grids)
+
+
+SMALL = [  # (M, P, tile, variant): ragged tiles, P = M, large support, small tiles
+    (20, 8, 8, 0), (16, 4, 8, 0), (18, 10, 8, 0), (24, 12, 4, 0), (12, 12, 8, 0),
+    (32, 16, 8, 0), (10, 2, 4, 0), (28, 6, 5, 0),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("M,P,tile,variant", SMALL)
+def test_stage_parity_small(prec, M, P, tile, variant):
+    """Spread grid, scaled grid, potential, force and energy, stage by stage."""
+    L, xi = 2.0, 4.0
+    dtype = np.float64 if prec == "fp64" else np.float32
+    x, q = systems.uniform_charges(301, L, seed=M * 100 + P, dtype=dtype)
+    q = q.astype(np.float64)
+    q[-1] = -q[:-1].sum()   # neutral with an odd count
+    q = q.astype(dtype)
+    g = run_gpu(x, q, L, xi, M, P, prec, grids=True, tile=tile, spread_variant=variant)
+    r = oracle_for(x, q, L, xi, M, P, prec, grids=True)
+    tol = TOL[prec]
+    assert rel(g["H"], r["H"]) < tol, "spread grid"
+    assert rel(g["Ht"], r["Ht"]) < 5 * tol, "scaled grid"
+    assert rel(g["phi"], r["phi"]) < 5 * tol, "phi"
+    assert rel(g["F"], r["F"]) < 5 * tol, "F"
+    assert abs(g["E"] - r["E"]) < 5 * tol * abs(r["E"]), "E"
+    assert abs(g["E_grid"] - r["E_grid"]) < 5 * tol * abs(r["E_grid"]), "E_grid"
+
+
+@pytest.mark.parametrize("M,P", [(32, 16), (24, 20), (40, 24), (36, 18)])
+def test_fp64_direct_and_tiled_spread_agree(M, P):
+    """Both spreading variants give the oracle's grid (FP64)."""
+    L, xi = 3.0, 3.5
+    x, q = systems.uniform_charges(500, L, seed=P)
+    r = oracle_for(x, q, L, xi, M, P, "fp64", grids=True)
+    for variant in (1, 2):
+        g = run_gpu(x, q, L, xi, M, P, "fp64", grids=True, spread_variant=variant)
+        assert rel(g["H"], r["H"]) < 1e-12, variant
+        assert rel(g["F"], r["F"]) < 1e-11, variant
+
+
+def test_grid_energy_equals_gather_energy():
+    L, xi, M, P = 2.0, 4.0, 20, 8
+    x, q = systems.uniform_charges(200, L, seed=5)
+    g = run_gpu(x, q, L, xi, M, P, "fp64", grids=True)
+    assert abs(g["E"] - g["E_grid"]) < 1e-12 * abs(g["E"])
+
+
+def test_empty_system():
+    plan = se.Plan(0, 2.0, 4.0, 16, 4, precision="fp64")
+    xd = torch.empty((0, 3), dtype=torch.float64, device="cuda")
+    qd = torch.empty((0,), dtype=torch.float64, device="cuda")
+    E, F, phi = plan.energy_force(xd, qd)
+    assert E == 0.0 and F.shape == (0, 3)
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_single_charge_nonneutral_warning(prec):
+    """A lone charge is non-neutral: status SE_WARN_NONNEUTRAL, results still
+    those of the method with k = 0 dropped."""
+    L, xi, M, P = 2.0, 4.0, 16, 8
+    dtype = np.float64 if prec == "fp64" else np.float32
+    x = np.array([[0.3, 1.1, 1.7]], dtype=dtype)
+    q = np.array([1.0], dtype=dtype)
+    g = run_gpu(x, q, L, xi, M, P, prec)
+    assert g["status"] == nat.SE_WARN_NONNEUTRAL
+    r = oracle_for(x, q, L, xi, M, P, prec)
+    assert abs(g["E"] - r["E"]) < 5 * TOL[prec] * abs(r["E"])
+    # a single charge feels no force from its own periodic images by symmetry
+    # only up to the SE approximation; compare with the oracle instead
+    assert np.abs(g["F"] - r["F"]).max() < 5 * TOL[prec] * max(1.0, np.abs(r["F"]).max())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_positions_outside_box_are_wrapped(prec):
+    L, xi, M, P = 2.0, 4.0, 20, 8
+    dtype = np.float64 if prec == "fp64" else np.float32
+    x, q = systems.uniform_charges(100, L, seed=7, dtype=dtype)
+    shift = np.zeros_like(x)
+    shift[::3, 0] = L
+    shift[1::3, 1] = -3 * L
+    shift[2::3, 2] = 2 * L
+    xs = (x + shift).astype(dtype)
+    g = run_gpu(xs, q, L, xi, M, P, prec)
+    r = oracle_for(xs, q, L, xi, M, P, prec)   # the oracle wraps the same way
+    assert rel(g["F"], r["F"]) < 5 * TOL[prec]
+    assert abs(g["E"] - r["E"]) < 5 * TOL[prec] * abs(r["E"])
+
+
+def test_cell_boundary_positions():
+    """Particles exactly on grid planes (x = i h) and at L - ulp use the
+    half-open cell rule on both sides."""
+    L, xi, M, P = 2.0, 4.0, 16, 8
+    h = L / M
+    x = np.array([[3 * h, 5 * h, 0.0], [np.nextafter(L, 0), 0.5, 7 * h],
+                  [0.0, 0.0, 0.0], [8 * h, np.nextafter(8 * h, 0), 1.0]])
+    q = np.array([1.0, -1.0, 0.5, -0.5])
+    g = run_gpu(x, q, L, xi, M, P, "fp64")
+    r = oracle_for(x, q, L, xi, M, P, "fp64")
+    assert rel(g["F"], r["F"]) < 1e-12
+    assert abs(g["E"] - r["E"]) < 1e-12 * abs(r["E"])
+
+
+def test_nonfinite_input_is_reported():
+    L, xi, M, P = 2.0, 4.0, 16, 8
+    x, q = systems.uniform_charges(10, L, seed=8)
+    x[3, 1] = np.nan
+    plan = se.Plan(10, L, xi, M, P)
+    xd = torch.tensor(x, device="cuda")
+    qd = torch.tensor(q, device="cuda")
+    with pytest.raises(nat.SEError) as e:
+        plan.energy_force(xd, qd)
+    assert e.value.status == nat.SE_ERR_NONFINITE
+    # the plan stays usable
+    x[3, 1] = 0.5
+    E, F, phi = plan.energy_force(torch.tensor(x, device="cuda"), qd)
+    assert math.isfinite(E)
+    plan.close()
+
+
+def test_prefactor_and_host_api():
+    L, xi, M, P = 2.0, 4.0, 20, 8
+    x, q = systems.uniform_charges(64, L, seed=9)
+    g1 = run_gpu(x, q, L, xi, M, P, "fp64")
+    kc = 138.935458
+    g2 = run_gpu(x, q, L, xi, M, P, "fp64", prefactor=kc)
+    assert abs(g2["E"] - kc * g1["E"]) < 1e-12 * abs(g2["E"])
+    assert rel(g2["F"], kc * g1["F"]) < 1e-13
+    plan = se.Plan(len(q), L, xi, M, P)
+    E, F, phi = plan.energy_force_host(x, q)
+    assert abs(E - g1["E"]) < 1e-13 * abs(E)
+    assert rel(F, g1["F"]) < 1e-14 and rel(phi, g1["phi"]) < 1e-14
+    plan.close()
+
+
+def test_repeated_calls_and_streams():
+    """Repeated evaluations (tile counters and tickets reset themselves) and a
+    non-default stream give the same result."""
+    L, xi, M, P = 2.0, 4.0, 20, 8
+    x, q = systems.uniform_charges(150, L, seed=10)
+    plan = se.Plan(len(q), L, xi, M, P)
+    xd = torch.tensor(x, device="cuda")
+    qd = torch.tensor(q, device="cuda")
+    E0, F0, _ = plan.energy_force(xd, qd)
+    F0 = F0.clone()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(5):
+            E1, F1, _ = plan.energy_force(xd, qd)
+    torch.cuda.synchronize()
+    assert abs(E1 - E0) < 1e-13 * abs(E0)
+    assert rel(F1.cpu().numpy(), F0.cpu().numpy()) < 1e-13
+    plan.close()
+
+
+# ---------------------------------------------------------------------------
+# the named workloads at full size
+# ---------------------------------------------------------------------------
+
+def _o1_sample(x, q, L, xi, idx, tol=1e-14):
+    nmax = oracle.nmax_for(xi, L, tol)
+    S = oracle.ewald_structure(x, q, L, nmax)
+    return oracle.ewald_eval(x[idx], q[idx], S, L, xi, nmax)
+
+
+@pytest.mark.parametrize("name", ["uniform-1000-L3-M32-P16-fp64", "water-L6-M52-P6-fp32comp",
+                                  "water-L6-M96-P24-fp64"])
+def test_workload_parity(name):
+    """Full-size workloads: elementwise against O2, and the accuracy against
+    the direct Ewald sum O1 (all particles)."""
+    x, q, w = systems.make(name)
+    prec = "fp64" if w["prec"] == "fp64" else "fp32"
+    g = run_gpu(x, q, w["L"], w["xi"], w["M"], w["P"], prec)
+    xd, qd = np.asarray(x, np.float64), np.asarray(q, np.float64)
+    r = oracle_for(xd, qd, w["L"], w["xi"], w["M"], w["P"], prec)
+    assert rel(g["F"], r["F"]) < 5 * TOL[prec]
+    assert rel(g["phi"], r["phi"]) < 5 * TOL[prec]
+    assert abs(g["E"] - r["E"]) < 5 * TOL[prec] * abs(r["E"])
+    # against the exact Ewald k-space sum
+    E1, phi1, F1 = oracle.ewald_kspace(xd, qd, w["L"], w["xi"])
+    e_gpu, e_o2 = rel(g["F"], F1), rel(r["F"], F1)
+    # the GPU result is as accurate as the FP64 SE it implements
+    assert e_gpu < e_o2 * 1.01 + 5 * TOL[prec]
+    if name.startswith("water-L6-M52-P6"):
+        # P = 6 misses the stated 1e-3 (measured 3.0e-3); P = 8 meets it
+        assert e_gpu < 4e-3
+    else:
+        assert e_gpu < w["target_rel_force_err"], e_gpu
+
+
+def test_water_P8_meets_1e3_target():
+    """The smallest even P that meets the stated 1e-3 for the L = 6 water box
+    (M = 52, FP32) is 8."""
+    x, q, w = systems.make("water-L6-M52-P6-fp32comp")
+    g = run_gpu(x, q, w["L"], w["xi"], w["M"], 8, "fp32")
+    xd, qd = np.asarray(x, np.float64), np.asarray(q, np.float64)
+    idx = np.arange(0, len(q), 37)
+    phi1, F1 = _o1_sample(xd, qd, w["L"], w["xi"], idx)
+    assert rel(g["F"][idx], F1) < 1e-3
+
+
+def test_workload_water_100k_fp32():
+    """L = 10 water box (100 200 atoms), M = 84, P = 8, FP32: elementwise
+    against O2 and against O1 on sampled atoms."""
+    x, q, w = systems.make("water-L10-M84-P8-fp32comp")
+    g = run_gpu(x, q, w["L"], w["xi"], w["M"], w["P"], "fp32")
+    xd, qd = np.asarray(x, np.float64), np.asarray(q, np.float64)
+    r = oracle_for(xd, qd, w["L"], w["xi"], w["M"], w["P"], "fp32")
+    assert rel(g["F"], r["F"]) < 5 * TOL["fp32"]
+    assert abs(g["E"] - r["E"]) < 5 * TOL["fp32"] * abs(r["E"])
+    idx = np.random.default_rng(0).choice(len(q), 64, replace=False)
+    phi1, F1 = _o1_sample(xd, qd, w["L"], w["xi"], idx, tol=1e-12)
+    assert rel(g["F"][idx], F1) < w["target_rel_force_err"]
