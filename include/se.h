@@ -63,6 +63,7 @@ extern "C" {
 #define SE_FP32 1   /* single precision with compensated (two-sum) grid
                        accumulation; Green's function table, grid energy and
                        the final energy reduction in double precision */
+#define SE_FP32_PLAIN 2  /* as SE_FP32 without the compensation of the grid sums */
 
 typedef struct se_plan se_plan;
 
@@ -77,7 +78,7 @@ int se_plan_create(se_plan **out, int64_t N, double L, double xi, int M, int P);
 /* Release every resource of the plan (NULL is accepted). */
 int se_plan_destroy(se_plan *plan);
 
-/* SE_FP64 (default) or SE_FP32. */
+/* SE_FP64 (default), SE_FP32 or SE_FP32_PLAIN. */
 int se_plan_set_precision(se_plan *plan, int prec);
 
 /* Shape of the Gaussian (Eq. 4.2): is_eta = 0 sets c (default 0.95), 1 sets
@@ -92,7 +93,7 @@ int se_plan_set_prefactor(se_plan *plan, double kc);
 int se_plan_set_stream(se_plan *plan, void *stream);
 
 /* Kernel tuning: spread_variant 0 = automatic, 1 = shared-memory tiles,
- * 2 = direct global accumulation (FP64 only); tile = edge of a spreading tile
+ * 2 = direct global accumulation (not with SE_FP32); tile = edge of a spreading tile
  * in grid cells (0 = automatic, else 2..32).  For benchmarking and tests. */
 int se_plan_set_tuning(se_plan *plan, int spread_variant, int tile);
 
@@ -129,6 +130,24 @@ int se_gather(se_plan *plan, const void *xyz, const void *q, void *phi, void *F,
  * SE_ERR_NONFINITE for NaN/Inf input. */
 int se_energy_force(se_plan *plan, const void *xyz, const void *q, double *E,
                     void *F, void *phi);
+
+/* The whole evaluation with every result on the device and no host
+ * synchronisation: F, phi and E (one double, E = 1/2 sum q phi) are device
+ * pointers and may each be NULL.  Status checks (non-neutral, non-finite)
+ * are kept on the device; read them with se_plan_get_status. */
+int se_evaluate(se_plan *plan, const void *xyz, const void *q, void *F, void *phi,
+                double *E);
+
+/* Status of the last evaluation's input checks (SE_OK, SE_WARN_NONNEUTRAL or
+ * SE_ERR_NONFINITE) into *status; waits for the plan's stream. */
+int se_plan_get_status(se_plan *plan, int *status);
+
+/* enable = 1 (default): se_evaluate, se_energy_force and se_energy_force_host
+ * replay one CUDA graph of the whole evaluation, captured at the first call
+ * and again whenever an argument pointer or the prefactor changes.  The
+ * graph is not used while the plan's stream is itself being captured, nor
+ * while stage timing is on.  enable = 0 launches every kernel directly. */
+int se_plan_set_graph(se_plan *plan, int enable);
 
 /* As se_energy_force but every array is in HOST memory: the call copies xyz
  * and q to the device, evaluates, and copies F, phi and E back before it

@@ -21,6 +21,7 @@ SE_ERR_CUFFT = -5
 SE_ERR_NONFINITE = -6
 SE_FP64 = 0
 SE_FP32 = 1
+SE_FP32_PLAIN = 2
 
 # name -> (restype, argtypes)
 _vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
@@ -41,6 +42,9 @@ SIGNATURES = {
     "se_energy_force_host": (_i, [_vp, _vp, _vp, _dp, _vp, _vp]),
     "se_copy_grid": (_i, [_vp, _i, _vp]),
     "se_self_energy": (_i, [_vp, _vp, _i64, _dp]),
+    "se_evaluate": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "se_plan_get_status": (_i, [_vp, ctypes.POINTER(_i)]),
+    "se_plan_set_graph": (_i, [_vp, _i]),
     "se_plan_set_timing": (_i, [_vp, _i]),
     "se_plan_get_timing": (_i, [_vp, _dp, _i, ctypes.POINTER(_i64), _i]),
     "se_strerror": (ctypes.c_char_p, [_i]),

@@ -93,6 +93,8 @@ __host__ __device__ constexpr int pick_d(int P) {
     return P;
 }
 
+constexpr int kScanSmem = 8192;   // tile counts staged in shared memory by the scan
+
 __device__ __forceinline__ int wrap_index(int i, int M) {
     i %= M;
     return i < 0 ? i + M : i;
@@ -125,6 +127,15 @@ __device__ __forceinline__ bool last_block(unsigned* ticket) {
     __syncthreads();
     if (is_last) __threadfence();
     return is_last;
+}
+
+// Sum of n partials (stride apart, from offset), by the whole block; valid in
+// thread 0.  The loads go through L2 (other blocks wrote them).
+__device__ __forceinline__ double sum_partials(const double* partials, int n, int stride,
+                                               int offset, double* sbuf) {
+    double v = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) v += __ldcg(partials + k * stride + offset);
+    return block_sum(v, sbuf);
 }
 
 // ---------------------------------------------------------------------------
@@ -164,24 +175,30 @@ k_bin(const T* __restrict__ xyz, const T* __restrict__ q, const KParams<T> kp,
     if (!last_block(ticket)) return;
 
     // --- last block: checks, exclusive scan of the tile counts ---
-    if (threadIdx.x == 0) {
-        double a = 0, b = 0, c = 0;
-        for (unsigned k = 0; k < gridDim.x; ++k) {
-            a += __ldcg(partials + 3 * k);
-            b += __ldcg(partials + 3 * k + 1);
-            c += __ldcg(partials + 3 * k + 2);
+    {
+        const double a = sum_partials(partials, gridDim.x, 3, 0, sbuf);
+        const double b = sum_partials(partials, gridDim.x, 3, 1, sbuf);
+        const double c = sum_partials(partials, gridDim.x, 3, 2, sbuf);
+        if (threadIdx.x == 0) {
+            acc->sum_q = a;
+            acc->sum_absq = b;
+            acc->nonfinite = (unsigned)c;
+            *ticket = 0u;
         }
-        acc->sum_q = a;
-        acc->sum_absq = b;
-        acc->nonfinite = (unsigned)c;
-        *ticket = 0u;
     }
     __shared__ int warp_tot[32];
+    __shared__ int scount[kScanSmem];
     const int n = kp.ntiles;
+    const bool staged = n <= kScanSmem;
+    if (staged) {
+        // one coalesced pass over the counts (written by atomics in L2)
+        for (int k = threadIdx.x; k < n; k += blockDim.x) scount[k] = __ldcg(tile_count + k);
+        __syncthreads();
+    }
     const int per = (n + blockDim.x - 1) / blockDim.x;
     const int b0 = min(n, (int)threadIdx.x * per), b1 = min(n, b0 + per);
     int local = 0;
-    for (int k = b0; k < b1; ++k) local += __ldcg(tile_count + k);
+    for (int k = b0; k < b1; ++k) local += staged ? scount[k] : __ldcg(tile_count + k);
     // block exclusive scan of `local`
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int incl = local;
@@ -205,11 +222,11 @@ k_bin(const T* __restrict__ xyz, const T* __restrict__ q, const KParams<T> kp,
     __syncthreads();
     int run = incl - local + (warp > 0 ? warp_tot[warp - 1] : 0);
     for (int k = b0; k < b1; ++k) {
-        int cnt = __ldcg(tile_count + k);
+        int cnt = staged ? scount[k] : __ldcg(tile_count + k);
         tile_start[k] = run;
         run += cnt;
-        tile_count[k] = 0;
     }
+    for (int k = threadIdx.x; k < n; k += blockDim.x) tile_count[k] = 0;
     if (threadIdx.x == blockDim.x - 1) tile_start[n] = run;
 }
 
@@ -446,9 +463,8 @@ k_scale(C* __restrict__ cgrid, const double* __restrict__ green, int M, double i
     double r = block_sum(e, sbuf);
     if (threadIdx.x == 0) partials[blockIdx.x] = r;
     if (!last_block(ticket)) return;
+    const double s = sum_partials(partials, gridDim.x, 1, 0, sbuf);
     if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (unsigned k = 0; k < gridDim.x; ++k) s += __ldcg(partials + k);
         acc->e_grid = s;
         if (E_out) *E_out = e_scale * s;
         *ticket = 0u;
@@ -581,9 +597,8 @@ k_gather(const v4_t<T>* __restrict__ sorted, const int* __restrict__ perm,
     double r = block_sum(e_loc, sbuf);
     if (threadIdx.x == 0) partials[blockIdx.x] = r;
     if (!last_block(ticket)) return;
+    const double s = sum_partials(partials, gridDim.x, 1, 0, sbuf);
     if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (unsigned k2 = 0; k2 < gridDim.x; ++k2) s += __ldcg(partials + k2);
         acc->e_gather = s;
         if (E_out) *E_out = e_scale * s;
         *ticket = 0u;

@@ -80,6 +80,13 @@ struct se_plan {
     int ev_next = 0;
     double stage_ms[kStages] = {};
     int64_t stage_count = 0;
+
+    // CUDA graph of one whole evaluation, replayed while its arguments match
+    bool use_graph = true;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    const void* gkey[5] = {};
+    double gkey_kc = 0.0;
 };
 
 namespace {
@@ -147,7 +154,7 @@ void derive(se_plan* p) {
     // spreading variant and tile edge
     int variant = p->tune_variant;
     if (variant == 0) variant = (p->prec == SE_FP64 && p->P > 12) ? 2 : 1;
-    if (p->prec != SE_FP64) variant = 1;  // the compensated sum needs the tiles
+    if (p->prec == SE_FP32) variant = 1;  // the compensated sum needs the tiles
     p->variant = variant;
     int tile = p->tune_tile > 0 ? p->tune_tile : 8;
     if (tile > p->M) tile = p->M;
@@ -156,7 +163,13 @@ void derive(se_plan* p) {
     p->ntiles = p->nT * p->nT * p->nT;
 }
 
+void drop_graph(se_plan* p) {
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+}
+
 void release_device(se_plan* p) {
+    drop_graph(p);
     if (p->have_fft) {
         cufftDestroy(p->fwd);
         cufftDestroy(p->inv);
@@ -313,7 +326,7 @@ int do_spread(se_plan* p, const void* xyz, const void* q) {
             SE_CUDA(se::launch_spread_direct<T>((const V*)p->sorted, (T*)p->grid_spread, kp, p->stream));
         else
             SE_CUDA(se::launch_spread_tiled<T>((const V*)p->sorted, p->tile_start, (T*)p->grid_spread,
-                                               kp, p->prec != SE_FP64, p->stream));
+                                               kp, p->prec == SE_FP32, p->stream));
     }
     timing_mark(p, 2);
     p->spread_clean = false;
@@ -376,6 +389,70 @@ int evaluate(se_plan* p, const void* xyz, const void* q, void* F, void* phi, dou
     return SE_OK;
 }
 
+// One evaluation as a replayed CUDA graph: captured on a private stream the
+// first time (and whenever an argument pointer or the prefactor changes),
+// then launched on the plan's stream.  Returns SE_ERR_UNSUPPORTED when the
+// graph cannot be used (the caller then launches directly).
+int graph_evaluate(se_plan* p, const void* xyz, const void* q, void* F, void* phi, double* dE) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(p->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return SE_ERR_UNSUPPORTED;  // the caller is capturing: launch into its capture
+    const void* key[5] = {xyz, q, F, phi, dE};
+    bool match = p->gexec && p->gkey_kc == p->kc;
+    for (int i = 0; i < 5 && match; ++i) match = key[i] == p->gkey[i];
+    if (!match) {
+        drop_graph(p);
+        if (!p->cap_stream)
+            SE_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+        if (!p->spread_clean) {
+            const size_t M3 = (size_t)p->M * p->M * p->M;
+            SE_CUDA(cudaMemsetAsync(p->grid_spread, 0, M3 * tsize(p->prec), p->stream));
+            p->spread_clean = true;
+        }
+        // the capture stream must see the state the user stream has reached
+        SE_CUDA(cudaStreamSynchronize(p->stream));
+        cudaStream_t user = p->stream;
+        p->stream = p->cap_stream;
+        const bool timing = p->timing;
+        p->timing = false;
+        cudaGraph_t g = nullptr;
+        int rc = check_cuda(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+        if (rc == SE_OK) {
+            rc = evaluate(p, xyz, q, F, phi, dE);
+            cudaError_t e = cudaStreamEndCapture(p->cap_stream, &g);
+            if (rc == SE_OK && e != cudaSuccess) rc = SE_ERR_CUDA;
+        }
+        p->stream = user;
+        p->timing = timing;
+        if (rc == SE_OK && cudaGraphInstantiate(&p->gexec, g, 0) != cudaSuccess) {
+            p->gexec = nullptr;
+            rc = SE_ERR_CUDA;
+        }
+        if (g) cudaGraphDestroy(g);
+        if (rc != SE_OK) {
+            cudaGetLastError();
+            p->gexec = nullptr;
+            return rc;
+        }
+        for (int i = 0; i < 5; ++i) p->gkey[i] = key[i];
+        p->gkey_kc = p->kc;
+    }
+    SE_CUDA(cudaGraphLaunch(p->gexec, p->stream));
+    p->spread_clean = true;
+    p->have_spread = p->have_scale = true;
+    return SE_OK;
+}
+
+// evaluate() through the graph when allowed, else by direct launches.
+int run_eval(se_plan* p, const void* xyz, const void* q, void* F, void* phi, double* dE) {
+    if (p->use_graph && !p->timing) {
+        int rc = graph_evaluate(p, xyz, q, F, phi, dE);
+        if (rc == SE_OK) return rc;
+        if (rc != SE_ERR_UNSUPPORTED) p->use_graph = false;  // capture failed: stop trying
+    }
+    return evaluate(p, xyz, q, F, phi, dE);
+}
+
 }  // namespace
 
 extern "C" {
@@ -411,6 +488,11 @@ int se_plan_destroy(se_plan* p) {
             for (int s = 0; s <= se_plan::kStages; ++s) cudaEventDestroy(p->ev[i][s]);
         p->ev_created = false;
     }
+    if (p->cap_stream) {
+        drop_graph(p);
+        cudaStreamDestroy(p->cap_stream);
+        p->cap_stream = nullptr;
+    }
     int cur = -1;
     if (p->ready && cudaGetDevice(&cur) == cudaSuccess && cur != p->device) {
         cudaSetDevice(p->device);
@@ -424,7 +506,7 @@ int se_plan_destroy(se_plan* p) {
 }
 
 int se_plan_set_precision(se_plan* p, int prec) {
-    if (!p || (prec != SE_FP64 && prec != SE_FP32)) return SE_ERR_ARG;
+    if (!p || (prec != SE_FP64 && prec != SE_FP32 && prec != SE_FP32_PLAIN)) return SE_ERR_ARG;
     if (prec != p->prec) {
         p->prec = prec;
         invalidate(p);
@@ -465,7 +547,7 @@ int se_plan_set_stream(se_plan* p, void* stream) {
 int se_plan_set_tuning(se_plan* p, int spread_variant, int tile) {
     if (!p || spread_variant < 0 || spread_variant > 2 || (tile != 0 && (tile < 2 || tile > 32)))
         return SE_ERR_ARG;
-    if (spread_variant == 2 && p->prec != SE_FP64) return SE_ERR_UNSUPPORTED;
+    if (spread_variant == 2 && p->prec == SE_FP32) return SE_ERR_UNSUPPORTED;
     p->tune_variant = spread_variant;
     p->tune_tile = tile;
     invalidate(p);
@@ -508,7 +590,7 @@ int se_gather(se_plan* p, const void* xyz, const void* q, void* phi, void* F, do
 int se_energy_force(se_plan* p, const void* xyz, const void* q, double* E, void* F, void* phi) {
     if (!p || (p->N > 0 && (!xyz || !q))) return SE_ERR_ARG;
     SE_TRY(prepare(p));
-    SE_TRY(evaluate(p, xyz, q, F, phi, p->dE));
+    SE_TRY(run_eval(p, xyz, q, F, phi, p->dE));
     if (E) {
         Acc a;
         SE_CUDA(cudaMemcpyAsync(&a, p->acc, sizeof(Acc), cudaMemcpyDeviceToHost, p->stream));
@@ -535,7 +617,7 @@ int se_energy_force_host(se_plan* p, const void* xyz, const void* q, double* E, 
         SE_CUDA(cudaMemcpyAsync(p->h_xyz, xyz, 3 * N * ts, cudaMemcpyHostToDevice, p->stream));
         SE_CUDA(cudaMemcpyAsync(p->h_q, q, N * ts, cudaMemcpyHostToDevice, p->stream));
     }
-    SE_TRY(evaluate(p, p->h_xyz, p->h_q, F ? p->h_F : nullptr, phi ? p->h_phi : nullptr, p->dE));
+    SE_TRY(run_eval(p, p->h_xyz, p->h_q, F ? p->h_F : nullptr, phi ? p->h_phi : nullptr, p->dE));
     if (N > 0 && F) SE_CUDA(cudaMemcpyAsync(F, p->h_F, 3 * N * ts, cudaMemcpyDeviceToHost, p->stream));
     if (N > 0 && phi) SE_CUDA(cudaMemcpyAsync(phi, p->h_phi, N * ts, cudaMemcpyDeviceToHost, p->stream));
     Acc a;
@@ -543,6 +625,32 @@ int se_energy_force_host(se_plan* p, const void* xyz, const void* q, double* E, 
     SE_CUDA(cudaStreamSynchronize(p->stream));
     if (E) *E = 0.5 * a.e_gather;
     return status_from_acc(a);
+}
+
+int se_evaluate(se_plan* p, const void* xyz, const void* q, void* F, void* phi, double* E) {
+    if (!p || (p->N > 0 && (!xyz || !q))) return SE_ERR_ARG;
+    SE_TRY(prepare(p));
+    return run_eval(p, xyz, q, F, phi, E);
+}
+
+int se_plan_set_graph(se_plan* p, int enable) {
+    if (!p) return SE_ERR_ARG;
+    p->use_graph = enable != 0;
+    if (!p->use_graph) drop_graph(p);
+    return SE_OK;
+}
+
+int se_plan_get_status(se_plan* p, int* status) {
+    if (!p || !status) return SE_ERR_ARG;
+    if (!p->ready) {
+        *status = SE_OK;
+        return SE_OK;
+    }
+    Acc a;
+    SE_CUDA(cudaMemcpyAsync(&a, p->acc, sizeof(Acc), cudaMemcpyDeviceToHost, p->stream));
+    SE_CUDA(cudaStreamSynchronize(p->stream));
+    *status = status_from_acc(a);
+    return SE_OK;
 }
 
 int se_copy_grid(se_plan* p, int which, void* dst) {

@@ -11,9 +11,10 @@ import torch
 
 from . import _native as nat
 
-PRECISIONS = {"fp64": nat.SE_FP64, "fp32": nat.SE_FP32}
-_TORCH_DTYPE = {nat.SE_FP64: torch.float64, nat.SE_FP32: torch.float32}
-_NP_DTYPE = {nat.SE_FP64: np.float64, nat.SE_FP32: np.float32}
+PRECISIONS = {"fp64": nat.SE_FP64, "fp32": nat.SE_FP32, "fp32plain": nat.SE_FP32_PLAIN}
+_TORCH_DTYPE = {nat.SE_FP64: torch.float64, nat.SE_FP32: torch.float32,
+                nat.SE_FP32_PLAIN: torch.float32}
+_NP_DTYPE = {nat.SE_FP64: np.float64, nat.SE_FP32: np.float32, nat.SE_FP32_PLAIN: np.float32}
 
 
 def _ptr(t):
@@ -161,15 +162,21 @@ class Plan:
                   "se_plan_get_timing")
         return dict(zip(self.STAGES, list(ms))), n.value
 
-    def evaluate(self, xyz, q, F, phi=None, E=None):
-        """spread + scale + gather without any host synchronisation (E: optional
-        CUDA float64 tensor of one element)."""
+    def evaluate(self, xyz, q, F=None, phi=None, E=None):
+        """se_evaluate: the whole evaluation with results on the device and no
+        host synchronisation (E: optional CUDA float64 tensor of one element).
+        Arguments are not re-checked here (hot path)."""
         self._stream()
-        h = self._h
-        chk = nat.check
-        chk(self._lib.se_spread(h, _ptr(xyz), _ptr(q)), "se_spread")
-        chk(self._lib.se_scale(h, None), "se_scale")
-        chk(self._lib.se_gather(h, _ptr(xyz), _ptr(q), _ptr(phi), _ptr(F), _ptr(E)), "se_gather")
+        nat.check(self._lib.se_evaluate(self._h, _ptr(xyz), _ptr(q), _ptr(F), _ptr(phi), _ptr(E)),
+                  "se_evaluate")
+
+    def status(self):
+        st = ctypes.c_int()
+        nat.check(self._lib.se_plan_get_status(self._h, ctypes.byref(st)), "se_plan_get_status")
+        return st.value
+
+    def set_graph(self, enable=True):
+        nat.check(self._lib.se_plan_set_graph(self._h, int(bool(enable))), "se_plan_set_graph")
 
     def copy_grid(self, which):
         """0: spread grid H (valid after spread), 1: Ht (after scale); [M,M,M] tensor."""
