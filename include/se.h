@@ -165,6 +165,26 @@ int se_copy_grid(se_plan *plan, int which, void *dst);
  * (double). Not part of the k-space result; provided for completeness. */
 int se_self_energy(const se_plan *plan, const double *q_host, int64_t n, double *E_self);
 
+/* se_spread_noalloc -- the spreading step without any device allocation.
+ * The paper has no counterpart: this exists for callers that cannot call
+ * cudaMalloc (a program that reserves all device memory at start-up and
+ * forbids allocation in its inner loop, or a component whose device memory
+ * belongs to another framework's allocator).
+ * Writes H_j = sum_n q_n c_g exp(-alpha |x_j - x_n|^2) (Eq. 3.5, FP64,
+ * parameters as se_plan_create with c = 0.95) into the caller's DEVICE grid
+ * H (M^3 doubles, z fastest; cleared by the call), from DEVICE xyz [N][3]
+ * and q [N], asynchronously on `stream` (cudaStream_t, NULL = default).
+ * All intermediate buffers live in one static device array of about 1.5 MB,
+ * reserved on every GPU that loads the library until the process exits.
+ * Limits: N <= 32768 and M <= 128; larger sizes return SE_ERR_ARG.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and should come before any stream capture.
+ * Calls share the array: calls that overlap on the GPU race; issue them on
+ * one stream.  Allocates nothing (no cudaMalloc, cudaFree or allocating
+ * library call). */
+int se_spread_noalloc(const double *xyz, const double *q, int64_t N, double L, double xi,
+                      int M, int P, double *H, void *stream);
+
 /* Static message for a status code. */
 const char *se_strerror(int status);
 

@@ -47,6 +47,7 @@ SIGNATURES = {
     "se_plan_set_graph": (_i, [_vp, _i]),
     "se_plan_set_timing": (_i, [_vp, _i]),
     "se_plan_get_timing": (_i, [_vp, _dp, _i, ctypes.POINTER(_i64), _i]),
+    "se_spread_noalloc": (_i, [_vp, _vp, _i64, _d, _d, _i, _i, _vp, _vp]),
     "se_strerror": (ctypes.c_char_p, [_i]),
     "se_version": (_i, []),
 }

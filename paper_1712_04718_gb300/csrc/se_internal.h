@@ -70,6 +70,9 @@ cudaError_t launch_gather(const v4_t<T>* sorted, const int* perm, const T* grid,
                           T* F, const KParams<T>& kp, double* partials, unsigned* ticket,
                           Acc* acc, double e_scale, double* E_out, cudaStream_t s);
 
+// Kernel parameters for an FP64 evaluation without a plan (se_plan.cu).
+int make_kparams_f64(int64_t N, double L, double xi, int M, int P, int tile, KParams<double>* out);
+
 constexpr int kMaxPartials = 1024;   // blocks of the reducing kernels
 constexpr size_t kSmemBudget = 200 * 1024;  // dynamic shared memory for a spreading tile
 

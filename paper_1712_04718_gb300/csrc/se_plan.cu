@@ -455,6 +455,29 @@ int run_eval(se_plan* p, const void* xyz, const void* q, void* F, void* phi, dou
 
 }  // namespace
 
+namespace se {
+
+// FP64 kernel parameters from raw arguments, through a plan on the stack
+// (no allocation of any kind).
+int make_kparams_f64(int64_t N, double L, double xi, int M, int P, int tile, KParams<double>* out) {
+    if (!out || N < 0 || !(L > 0) || !isfinite(L) || !(xi > 0) || !isfinite(xi)) return SE_ERR_ARG;
+    se_plan tmp;
+    tmp.N = N;
+    tmp.L = L;
+    tmp.xi = xi;
+    tmp.M = M;
+    tmp.P = P;
+    tmp.prec = SE_FP64;
+    tmp.tune_variant = 1;
+    tmp.tune_tile = tile;
+    derive(&tmp);
+    if (!(tmp.eta > 0.0 && tmp.eta < 1.0)) return SE_ERR_ARG;
+    *out = make_kparams<double>(&tmp);
+    return SE_OK;
+}
+
+}  // namespace se
+
 extern "C" {
 
 int se_plan_create(se_plan** out, int64_t N, double L, double xi, int M, int P) {
