@@ -92,9 +92,13 @@ int se_plan_set_prefactor(se_plan *plan, double kc);
 /* CUDA stream (cudaStream_t) for every later call; NULL = legacy default. */
 int se_plan_set_stream(se_plan *plan, void *stream);
 
-/* Kernel tuning: spread_variant 0 = automatic, 1 = shared-memory tiles,
- * 2 = direct global accumulation (not with SE_FP32); tile = edge of a spreading tile
- * in grid cells (0 = automatic, else 2..32).  For benchmarking and tests. */
+/* Kernel tuning: spread_variant 0 = automatic, 1 = shared-memory tiles and
+ * cuFFT, 2 = direct global accumulation and cuFFT (not with SE_FP32),
+ * 3 = the single-precision pipeline without cuFFT (SE_FP32 or SE_FP32_PLAIN,
+ * M <= 128; the default there): exact 64-bit fixed-point spreading, line DFTs
+ * with the scaling fused into the x pass, kernels chained by programmatic
+ * dependent launch.  tile = edge of a spreading tile in grid cells
+ * (0 = automatic, else 2..32).  For benchmarking and tests. */
 int se_plan_set_tuning(se_plan *plan, int spread_variant, int tile);
 
 /* Derived parameters: out[0..9] = h, w, eta, alpha, c_g, m, tile edge,

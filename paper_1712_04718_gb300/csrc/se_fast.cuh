@@ -1,0 +1,544 @@
+// se_fast.cuh -- the single-precision SE pipeline for grids up to 128^3:
+// nine short kernels chained by programmatic dependent launch, no cuFFT.
+//
+//   k_fbin      tile of each particle, slot in its tile, q sums; clears the
+//               fixed-point spread grid
+//   k_fscatter  every block scans the tile counts; particles in tile order;
+//               block 0 publishes the tile offsets, the input checks and the
+//               fixed-point scale
+//   k_fspread   Eq. 3.5, one CTA per tile, exact 64-bit fixed-point sums in
+//               shared memory (two native 32-bit atomics per weight), flushed
+//               with global 64-bit integer reductions: the grid is the same
+//               for any order of the additions
+//   k_slab_fwd  per x-slab: forward DFT along z (real to complex; the
+//               fixed-point grid is converted to float here), then along y
+//   k_xpass     forward DFT along x, scaling by G(k)/M^3 (Eq. 3.6) with the
+//               grid energy, inverse DFT along x
+//   k_slab_inv  per x-slab: inverse DFT along y, then along z (complex to real)
+//   (k_gather from se_kernels.cuh reads the real grid)
+//
+// The 1-D transforms are direct DFTs (M <= 128) written as small complex
+// matrix products with register tiles (se_dft.cuh); twiddles e^{-2 pi i r/M}
+// from a table in shared memory.
+#pragma once
+#include "se_dft.cuh"
+#include "se_kernels.cuh"
+
+namespace se {
+
+constexpr int kFastKC = 8;        // spectrum columns per block in the y and x passes
+
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_fbin(const T* __restrict__ xyz, const T* __restrict__ q, const KParams<T> kp,
+       int* __restrict__ tile_count, int* __restrict__ slot, int* __restrict__ tile_of,
+       double* __restrict__ partials, long long* __restrict__ g64) {
+    SE_STAMP(0, 0);
+    pdl_wait();
+    pdl_launch_next();
+    SE_STAMP(0, 1);
+    __shared__ df2 sbuf[32];
+    __shared__ int sbad;
+    if (threadIdx.x == 0) sbad = 0;
+    const long long M3 = (long long)kp.M * kp.M * kp.M;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < M3; i += stride)
+        g64[i] = 0;
+    SE_STAMP(0, 2);
+    df2 sq = df_from(0.0f), sa = df_from(0.0f);
+    float qmax = 0.0f;
+    int bad = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kp.N; i += gridDim.x * blockDim.x) {
+        T x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2], qq = q[i];
+        if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(qq))) bad += 1;
+        T t;
+        int cx = cell_of(wrap_coord(x, kp.L, kp.invL), kp.invh, kp.M, &t);
+        int cy = cell_of(wrap_coord(y, kp.L, kp.invL), kp.invh, kp.M, &t);
+        int cz = cell_of(wrap_coord(z, kp.L, kp.invL), kp.invh, kp.M, &t);
+        int tile = ((cx / kp.tile) * kp.nT + cy / kp.tile) * kp.nT + cz / kp.tile;
+        slot[i] = atomicAdd(tile_count + tile, 1);
+        tile_of[i] = tile;
+        sq = df_add(sq, df_from((float)qq));
+        sa = df_add(sa, df_from(fabsf((float)qq)));
+        qmax = fmaxf(qmax, fabsf((float)qq));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) qmax = fmaxf(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
+    __shared__ unsigned smax;
+    if (threadIdx.x == 0) smax = 0u;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) atomicMax(&smax, __float_as_uint(qmax));   // |q| >= 0: bits order as values
+    SE_STAMP(0, 3);
+    if (bad) atomicAdd(&sbad, bad);
+    const df2 r0 = block_sum_df(sq, sbuf);
+    const df2 r1 = block_sum_df(sa, sbuf);
+    if (threadIdx.x == 0) {
+        // per block: q sum (hi, lo), |q| sum (hi, lo), non-finite count
+        float* pf = reinterpret_cast<float*>(partials);
+        pf[6 * blockIdx.x] = r0.hi;
+        pf[6 * blockIdx.x + 1] = r0.lo;
+        pf[6 * blockIdx.x + 2] = r1.hi;
+        pf[6 * blockIdx.x + 3] = r1.lo;
+        pf[6 * blockIdx.x + 4] = __int_as_float(sbad);
+        pf[6 * blockIdx.x + 5] = __uint_as_float(smax);
+    }
+    SE_STAMP(0, 4);
+}
+
+// Exclusive scan of n ints in shared memory (in place), by one block.
+__device__ __forceinline__ void block_scan_smem(int* s, int n) {
+    __shared__ int warp_tot[32];
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int b0 = min(n, (int)threadIdx.x * per), b1 = min(n, b0 + per);
+    int local = 0;
+    for (int k = b0; k < b1; ++k) local += s[k];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int nw = blockDim.x >> 5;
+        int v = lane < nw ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        if (lane < nw) warp_tot[lane] = v;
+    }
+    __syncthreads();
+    int run = incl - local + (warp > 0 ? warp_tot[warp - 1] : 0);
+    for (int k = b0; k < b1; ++k) {
+        int c = s[k];
+        s[k] = run;
+        run += c;
+    }
+    __syncthreads();
+}
+
+// Fixed-point scale 2^k for the spread: every weight is at most
+// B = c_g max|q| (the Gaussian factors are <= 1), and k = 40 - ceil(log2 B)
+// keeps each scaled weight below 2^40.  A sum of n weights stays below
+// n 2^40, far inside 64 bits for any particle count.
+__device__ __forceinline__ int fx_shift_for(double B) {
+    if (!(B > 0.0) || !isfinite(B)) return 40;
+    int e = (int)ceil(log2(B));
+    int k = 40 - e;
+    return k < -60 ? -60 : (k > 100 ? 100 : k);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_fscatter(const T* __restrict__ xyz, const T* __restrict__ q, const KParams<T> kp,
+           const int* __restrict__ tile_count, const int* __restrict__ slot,
+           const int* __restrict__ tile_of, int* __restrict__ tile_start,
+           v4_t<T>* __restrict__ sorted, int* __restrict__ perm,
+           const double* __restrict__ partials, int nbin_blocks, Acc* acc) {
+    SE_STAMP(1, 0);
+    pdl_wait();
+    pdl_launch_next();
+    SE_STAMP(1, 1);
+    __shared__ df2 sbuf[32];
+    __shared__ int s_start[kScanSmem + 1];
+    const int n = kp.ntiles;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) s_start[k] = tile_count[k];
+    __syncthreads();
+    block_scan_smem(s_start, n);
+    SE_STAMP(1, 2);
+    if (blockIdx.x == 0) {
+        for (int k = threadIdx.x; k < n; k += blockDim.x) tile_start[k] = s_start[k];
+        if (threadIdx.x == 0) tile_start[n] = kp.N;
+        const float* pf = reinterpret_cast<const float*>(partials);
+        const df2 a = sum_partials_df(pf, nbin_blocks, 3, 0, sbuf);
+        const df2 b = sum_partials_df(pf, nbin_blocks, 3, 1, sbuf);
+        int nbad = 0;
+        unsigned qm = 0u;
+        for (int k = threadIdx.x; k < nbin_blocks; k += blockDim.x) {
+            nbad += __float_as_int(__ldcg(pf + 6 * k + 4));
+            qm = max(qm, __float_as_uint(__ldcg(pf + 6 * k + 5)));
+        }
+        __shared__ int sb;
+        __shared__ unsigned sqm;
+        if (threadIdx.x == 0) {
+            sb = 0;
+            sqm = 0u;
+        }
+        __syncthreads();
+        if (nbad) atomicAdd(&sb, nbad);
+        atomicMax(&sqm, qm);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            acc->sum_q = df_to_double(a);
+            acc->sum_absq = df_to_double(b);
+            acc->nonfinite = (unsigned)sb;
+            const int k = fx_shift_for((double)kp.qcg * (double)__uint_as_float(sqm));
+            acc->fx_shift = k;
+            acc->fx_scale = ldexpf(1.0f, k);
+            acc->fx_inv = ldexpf(1.0f, -k);
+        }
+    }
+    SE_STAMP(1, 3);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kp.N; i += gridDim.x * blockDim.x) {
+        const int dst = s_start[tile_of[i]] + slot[i];
+        v4_t<T> v;
+        v.x = wrap_coord(xyz[3 * i], kp.L, kp.invL);
+        v.y = wrap_coord(xyz[3 * i + 1], kp.L, kp.invL);
+        v.z = wrap_coord(xyz[3 * i + 2], kp.L, kp.invL);
+        v.w = q[i];
+        sorted[dst] = v;
+        perm[dst] = i;
+    }
+    SE_STAMP(1, 4);
+}
+
+// A scaled weight v (float, |v| < 2^62) rounded to the nearest integer and
+// split into the two 32-bit words of its 64-bit two's complement, with FP32
+// and 32-bit integer operations only (no 64-bit conversion, which would run
+// on the FP64 pipe).  |v| < 2^31: one float-to-int32 conversion, the high
+// word is the sign.  |v| >= 2^31: v is already an integer and
+// v = hf 2^32 + lf exactly, with hf = floor(v 2^-32) and 0 <= lf < 2^32 a
+// multiple of v's ulp, so lf is exact in float.
+__device__ __forceinline__ void fx_split(float v, unsigned* vh, unsigned* vl) {
+    if (fabsf(v) < 2147483648.0f) {
+        const int vi = __float2int_rn(v);
+        *vl = (unsigned)vi;
+        *vh = (unsigned)(vi >> 31);
+    } else {
+        const float hf = floorf(v * 2.3283064365386963e-10f);   // 2^-32
+        const float lf = fmaf(-hf, 4294967296.0f, v);           // exact
+        *vl = __float2uint_rn(lf);
+        *vh = (unsigned)__float2int_rn(hf);
+    }
+}
+
+// One weight into a 64-bit fixed-point accumulator held as (hi, lo) 32-bit
+// words in shared memory: lo gets the low word and reports its carry, hi the
+// high word plus the carry.  Two's-complement addition modulo 2^64, exact and
+// independent of the order of the additions.
+__device__ __forceinline__ void fx_add(unsigned* hi, unsigned* lo, float v) {
+    unsigned vl, vh;
+    fx_split(v, &vh, &vl);
+    const unsigned old = atomicAdd(lo, vl);
+    const unsigned carry = (old + vl < old) ? 1u : 0u;
+    atomicAdd(hi, vh + carry);
+}
+
+// A scaled weight v (|v| < 2^40) rounded to an integer V and added as two
+// pieces to two 32-bit words with non-returning atomics: V mod 2^21 to the
+// first (unsigned) and floor(V / 2^21) to the second (signed).  No carry, so
+// no atomic waits on another.  The first word cannot overflow while a point
+// receives fewer than 2^11 weights, i.e. while a tile holds fewer than 2048
+// particles; the second (|piece| < 2^19) neither.  The split is exact in
+// FP32: V = rint(v) is exact for |v| < 2^24 and v is already an integer
+// beyond; floor(V 2^-21) is exact; V - 2^21 floor(V 2^-21) lies in [0, 2^21)
+// on V's ulp grid and is representable.
+__device__ __forceinline__ void fx_add2(unsigned* w0, unsigned* w1, float v) {
+    const float vr = rintf(v);
+    const float hf = floorf(vr * 4.76837158203125e-7f);   // 2^-21
+    const float lf = fmaf(-hf, 2097152.0f, vr);           // exact, in [0, 2^21)
+    atomicAdd(w0, __float2uint_rn(lf));
+    atomicAdd(w1, (unsigned)__float2int_rn(hf));
+}
+
+__device__ __forceinline__ unsigned long long fx_join2(unsigned a0, unsigned a1) {
+    return ((unsigned long long)(long long)(int)a1 << 21) + (unsigned long long)a0;
+}
+
+template <int P>
+__global__ void __launch_bounds__(256)
+k_fspread(const f4* __restrict__ sorted, const int* __restrict__ tile_start,
+          int* __restrict__ tile_count, unsigned long long* __restrict__ g64,
+          const KParams<float> kp, const Acc* __restrict__ acc, int slab) {
+    constexpr int D = pick_d(P), G = P / D, GPW = 32 / G;
+    SE_STAMP(2, 0);
+    pdl_wait();
+    pdl_launch_next();
+    SE_STAMP(2, 1);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned* hi = reinterpret_cast<unsigned*>(smem_raw);
+    __shared__ float sE3[P];
+    // the counters are consumed: clear them for the next evaluation
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < kp.ntiles; k += gridDim.x * blockDim.x)
+        tile_count[k] = 0;
+    const int tile = blockIdx.x;
+    const int pbeg = tile_start[tile], pend = tile_start[tile + 1];
+    if (pbeg == pend) return;
+    if (threadIdx.x < P) sE3[threadIdx.x] = kp.E3[threadIdx.x];
+    const float fxs = acc->fx_scale;
+    const int nT = kp.nT, M = kp.M, TT = kp.tile;
+    const int tz = tile % nT, ty = (tile / nT) % nT, tx = tile / (nT * nT);
+    const int t0x = tx * TT, t0y = ty * TT, t0z = tz * TT;
+    const int Ry = min(TT, M - t0y) + P - 1, Rz = min(TT, M - t0z) + P - 1;
+    const int Rx = min(TT, M - t0x) + P - 1;
+    const int plane = Ry * Rz;
+    unsigned* lo = hi + (size_t)slab * plane;
+    // fewer than 2048 particles: two carry-free pieces; else (hi, lo) with carries
+    const bool two = (pend - pbeg) < 2048;
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gi = lane / G, k = lane - gi * G;
+    const bool act = gi < GPW;
+    const int ngroups = (blockDim.x >> 5) * GPW;
+    const int group = warp * GPW + gi;
+
+    for (int s0 = 0; s0 < Rx; s0 += slab) {
+        const int ns = min(slab, Rx - s0);
+        const int nel = ns * plane;
+        for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+            hi[e] = 0u;
+            lo[e] = 0u;
+        }
+        __syncthreads();
+        SE_STAMP(2, 2);
+        if (act) {
+            for (int p = pbeg + group; p < pend; p += ngroups) {
+                const f4 v = sorted[p];
+                float t;
+                const int cx = cell_of(v.x, kp.invh, M, &t);
+                const float ux = centre_offset(t, cx);
+                const int cy = cell_of(v.y, kp.invh, M, &t);
+                const float uy = centre_offset(t, cy);
+                const int cz = cell_of(v.z, kp.invh, M, &t);
+                const float uz = centre_offset(t, cz);
+                const int lx = cx - t0x, ly = cy - t0y, lz = cz - t0z;
+                const int alo = max(0, s0 - lx), ahi = min(P, s0 + ns - lx);
+                if (alo >= ahi) continue;
+                float gy[P];
+                fgg<float, P>(uy, kp.beta, kp.E3, gy);
+                float gz[D];
+                const float qw = v.w * kp.qcg * fxs;
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    const float dz = float(k + j * G) - 0.5f * float(P - 1) - uz;
+                    gz[j] = qw * expf(-kp.beta * dz * dz);
+                }
+                const float Bx = expf(2.0f * kp.beta * ux);
+                float px = expf(-kp.beta * ux * (ux + float(P - 1)) + 2.0f * kp.beta * ux * float(alo));
+#pragma unroll 1
+                for (int a = alo; a < ahi; ++a) {
+                    const float gxa = px * sE3[a];
+                    px *= Bx;
+                    const int rowx = lx + a - s0;
+                    const int rowoff = (rowx * Ry + ly) * Rz + lz + k;
+#pragma unroll
+                    for (int b = 0; b < P; ++b) {
+                        const float wab = gxa * gy[b];
+#pragma unroll
+                        for (int j = 0; j < D; ++j) {
+                            const int e = rowoff + b * Rz + j * G;
+                            if (two)
+                                fx_add2(lo + e, hi + e, wab * gz[j]);
+                            else
+                                fx_add(hi + e, lo + e, wab * gz[j]);
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        SE_STAMP(2, 3);
+        const int ox = t0x - P / 2 + 1 + s0, oy = t0y - P / 2 + 1, oz = t0z - P / 2 + 1;
+        for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+            const unsigned long long v =
+                two ? fx_join2(lo[e], hi[e])
+                    : (((unsigned long long)hi[e] << 32) | (unsigned long long)lo[e]);
+            if (v != 0ull) {
+                const int rz = e % Rz, r = e / Rz;
+                const int ry = r % Ry, rx = r / Ry;
+                const int gx_ = wrap_index(ox + rx, M), gy_ = wrap_index(oy + ry, M),
+                          gz_ = wrap_index(oz + rz, M);
+                atomicAdd(g64 + ((size_t)gx_ * M + gy_) * M + gz_, v);
+            }
+        }
+        __syncthreads();
+        SE_STAMP(2, 4);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The 3-D transform in three kernels.  tw[r] = (cos, sin)(2 pi r / M); the
+// forward transform uses e^{-i}, the inverse e^{+i}; both unnormalised.
+//   k_slab_fwd  per x-slab: z real-to-complex, then y      (C[x][ky][kz])
+//   k_xpass     per (ky, kz-chunk): x forward, G(k)/M^3 and the grid energy,
+//               x inverse
+//   k_slab_inv  per x-slab: y inverse, then z complex-to-real (R[x][y][z])
+
+constexpr int kSlabThreads = 512;
+
+__device__ __forceinline__ void load_twiddles(float2* tw, const float2* __restrict__ tw_g, int M) {
+    for (int i = threadIdx.x; i < M; i += blockDim.x) tw[i] = tw_g[i];
+}
+
+// shared memory of the slab kernels: tw[M] | A: M x (M+1) floats, or the
+// M x Mh complex slab | T: Mh x (M+1) complex
+__host__ __device__ inline size_t slab_a_bytes(int M) {
+    const size_t Mh = M / 2 + 1, SP = M + 1;
+    const size_t a = (size_t)M * SP * sizeof(float), c = (size_t)M * Mh * sizeof(float2);
+    return ((a > c ? a : c) + 15) / 16 * 16;
+}
+__host__ __device__ inline size_t slab_smem_bytes(int M) {
+    const size_t Mh = M / 2 + 1, SP = M + 1;
+    return (size_t)M * sizeof(float2) + slab_a_bytes(M) + Mh * SP * sizeof(float2);
+}
+
+__global__ void __launch_bounds__(kSlabThreads)
+k_slab_fwd(const long long* __restrict__ g64, float2* __restrict__ C,
+           const float2* __restrict__ tw_g, int M, const Acc* __restrict__ acc) {
+    SE_STAMP(3, 0);
+    pdl_wait();
+    pdl_launch_next();
+    SE_STAMP(3, 1);
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int Mh = M / 2 + 1, SP = M + 1;
+    float2* tw = reinterpret_cast<float2*>(sm);
+    float* S = reinterpret_cast<float*>(sm + (size_t)M * sizeof(float2));
+    float2* T = reinterpret_cast<float2*>(sm + (size_t)M * sizeof(float2) + slab_a_bytes(M));
+    const int x = blockIdx.x;
+    load_twiddles(tw, tw_g, M);
+    const float inv = acc->fx_inv;
+    const long long* src = g64 + (size_t)x * M * M;
+    for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
+        const int y = e / M, z = e - y * M;
+        // int64 -> float through its two 32-bit words (no 64-bit conversion)
+        const unsigned long long u = (unsigned long long)src[e];
+        const float hi = (float)(int)(u >> 32), lo = (float)(unsigned)(u & 0xffffffffull);
+        S[y * SP + z] = fmaf(hi, 4294967296.0f, lo) * inv;
+    }
+    __syncthreads();
+    SE_STAMP(3, 2);
+    // z, real to complex: X(j = z, c = y) = S[y][z]  ->  T[kz][y]
+    dft_r2c<2, 2>(S, 1, SP, T, SP, 1, M, Mh, M, tw, M);
+    __syncthreads();
+    SE_STAMP(3, 3);
+    // y forward: X(j = y, c = kz) = T[kz][y]  ->  C[x][ky][kz]
+    dft_c2c<2, 2>(T, 1, SP, C + (size_t)x * M * Mh, Mh, 1, M, M, Mh, tw, M, -1.0f);
+    SE_STAMP(3, 4);
+}
+
+__global__ void __launch_bounds__(256)
+k_xpass(float2* __restrict__ C, const float2* __restrict__ tw_g, const float* __restrict__ green,
+        int M, float invM3, double* __restrict__ partials, unsigned* ticket, Acc* acc,
+        double e_scale, double* E_out) {
+    SE_STAMP(4, 0);
+    pdl_wait();
+    pdl_launch_next();
+    SE_STAMP(4, 1);
+    __shared__ float2 tw[kFastMaxM];
+    __shared__ float2 s[kFastMaxM * kFastKC];
+    __shared__ float2 s2[kFastMaxM * kFastKC];
+    __shared__ df2 sbuf[32];
+    const int Mh = M / 2 + 1;
+    const int nch = (Mh + kFastKC - 1) / kFastKC;
+    const int y = blockIdx.x / nch, c0 = (blockIdx.x % nch) * kFastKC;
+    const int nc = min(kFastKC, Mh - c0);
+    load_twiddles(tw, tw_g, M);
+    for (int e = threadIdx.x; e < M * nc; e += blockDim.x) {
+        const int x = e / nc, kk = e - x * nc;
+        s[x * kFastKC + kk] = C[((size_t)x * M + y) * Mh + c0 + kk];
+    }
+    __syncthreads();
+    SE_STAMP(4, 2);
+    dft_c2c<2, 2>(s, kFastKC, 1, s2, kFastKC, 1, M, M, nc, tw, M, -1.0f);
+    __syncthreads();
+    SE_STAMP(4, 3);
+    df2 en = df_from(0.0f);   // double-float energy sum
+    for (int e = threadIdx.x; e < M * nc; e += blockDim.x) {
+        const int kx = e / nc, kk = e - kx * nc;
+        const int kz = c0 + kk;
+        const float2 v = s2[kx * kFastKC + kk];
+        const float g = green[((size_t)kx * M + y) * Mh + kz];
+        en = df_add(en, df_from(((kz == 0 || 2 * kz == M) ? 1.0f : 2.0f) * g *
+                                fmaf(v.x, v.x, v.y * v.y)));
+        const float f = g * invM3;
+        s2[kx * kFastKC + kk] = make_float2(v.x * f, v.y * f);
+    }
+    __syncthreads();
+    dft_c2c<2, 2>(s2, kFastKC, 1, C + (size_t)y * Mh + c0, (size_t)M * Mh, 1, M, M, nc, tw, M, 1.0f);
+    SE_STAMP(4, 4);
+    float* pf = reinterpret_cast<float*>(partials);
+    const df2 tot = block_sum_df(en, sbuf);
+    if (threadIdx.x == 0) {
+        pf[2 * blockIdx.x] = tot.hi;
+        pf[2 * blockIdx.x + 1] = tot.lo;
+    }
+    const bool lastb = last_block(ticket);
+    SE_STAMP(4, 5);
+    if (!lastb) return;
+    const df2 sum = sum_partials_df(pf, gridDim.x, 1, 0, sbuf);
+    if (threadIdx.x == 0) {
+        const double e = df_to_double(sum);
+        acc->e_grid = e;
+        if (E_out) *E_out = e_scale * e;
+        *ticket = 0u;
+    }
+}
+
+__global__ void __launch_bounds__(kSlabThreads)
+k_slab_inv(const float2* __restrict__ C, float* __restrict__ R, const float2* __restrict__ tw_g,
+           int M) {
+    SE_STAMP(5, 0);
+    pdl_wait();
+    pdl_launch_next();
+    SE_STAMP(5, 1);
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int Mh = M / 2 + 1, SP = M + 1;
+    float2* tw = reinterpret_cast<float2*>(sm);
+    float* S = reinterpret_cast<float*>(sm + (size_t)M * sizeof(float2));
+    float2* A = reinterpret_cast<float2*>(S);   // the slab, before S is needed
+    float2* T = reinterpret_cast<float2*>(sm + (size_t)M * sizeof(float2) + slab_a_bytes(M));
+    const int x = blockIdx.x;
+    load_twiddles(tw, tw_g, M);
+    const float2* src = C + (size_t)x * M * Mh;
+    for (int e = threadIdx.x; e < M * Mh; e += blockDim.x) A[e] = src[e];
+    __syncthreads();
+    // y inverse: X(j = ky, c = kz) = A[ky][kz]  ->  T[kz][y], with the
+    // Hermitian weights of the z real transform (1 at kz = 0 and M/2, else 2)
+    dft_c2c<2, 2>(A, Mh, 1, T, 1, SP, M, M, Mh, tw, M, 1.0f);
+    __syncthreads();
+    SE_STAMP(5, 2);
+    for (int e = threadIdx.x; e < Mh * M; e += blockDim.x) {
+        const int kz = e / M, y = e - kz * M;
+        if (kz != 0 && 2 * kz != M) {
+            float2 v = T[kz * SP + y];
+            T[kz * SP + y] = make_float2(2.f * v.x, 2.f * v.y);
+        }
+    }
+    __syncthreads();
+    // z complex to real: X(j = kz, c = y) = T[kz][y]  ->  S[y][z]
+    dft_c2r<2, 2>(T, SP, 1, S, 1, SP, Mh, M, M, tw, M);
+    __syncthreads();
+    SE_STAMP(5, 3);
+    float* dst = R + (size_t)x * M * M;
+    for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
+        const int y = e / M, z = e - y * M;
+        dst[e] = S[y * SP + z];
+    }
+    SE_STAMP(5, 4);
+}
+
+}  // namespace se
+
+namespace se {
+
+// fixed-point grid -> real grid (for inspection of the spread grid)
+__global__ void __launch_bounds__(256)
+k_fx_to_real(const long long* __restrict__ g64, float* __restrict__ dst, long long n,
+             const Acc* __restrict__ acc) {
+    pdl_wait();
+    const float inv = acc->fx_inv;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+    {
+        const unsigned long long u = (unsigned long long)g64[i];
+        const float hi = (float)(int)(u >> 32), lo = (float)(unsigned)(u & 0xffffffffull);
+        dst[i] = fmaf(hi, 4294967296.0f, lo) * inv;
+    }
+}
+
+}  // namespace se

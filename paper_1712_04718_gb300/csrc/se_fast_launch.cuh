@@ -1,0 +1,138 @@
+// se_fast_launch.cuh -- host launchers of the single-precision pipeline
+// (se_fast.cuh).  Every kernel after the first is launched with programmatic
+// stream serialization: it may be scheduled while its predecessor drains and
+// waits for that predecessor's results in griddepcontrol.wait.
+#pragma once
+#include <algorithm>
+
+#include "se_fast.cuh"
+#include "se_launch.cuh"
+
+namespace se {
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_ex(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+                      bool pdl, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? attr : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+inline int fast_bin_blocks(const KParams<float>& kp) {
+    const long long m3 = (long long)kp.M * kp.M * kp.M;
+    long long b = std::max<long long>((kp.N + 255) / 256, (m3 + 2047) / 2048);
+    return (int)std::max<long long>(1, std::min<long long>(b, kMaxPartials));
+}
+
+template <int P>
+cudaError_t fast_spread_P(const KParams<float>& kp, const FastBufs& b, cudaStream_t s) {
+    const size_t R = (size_t)kp.tile + P - 1;
+    const size_t plane = R * R * 2 * sizeof(unsigned);
+    const int slab = (int)std::min(R, kSmemBudget / plane);
+    if (slab < 1) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_fspread<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSmemBudget);
+    if (e != cudaSuccess) return e;
+    return launch_ex(k_fspread<P>, kp.ntiles, kThreads, (size_t)slab * plane, s, true,
+                     (const f4*)b.sorted, (const int*)b.tile_start, b.tile_count,
+                     (unsigned long long*)b.g64, kp, (const Acc*)b.acc, slab);
+}
+
+cudaError_t fast_spread(const float* xyz, const float* q, const KParams<float>& kp,
+                        const FastBufs& b, cudaStream_t s) {
+    const int nbin = fast_bin_blocks(kp);
+    cudaError_t e = launch_ex(k_fbin<float>, nbin, kThreads, 0, s, false, xyz, q, kp, b.tile_count,
+                              b.slot, b.tile_of, b.partials, b.g64);
+    if (e != cudaSuccess) return e;
+    const int nsc = std::max(1, std::min((kp.N + kThreads - 1) / kThreads, 160));
+    e = launch_ex(k_fscatter<float>, nsc, kThreads, 0, s, true, xyz, q, kp,
+                  (const int*)b.tile_count, (const int*)b.slot, (const int*)b.tile_of, b.tile_start,
+                  (f4*)b.sorted, b.perm, (const double*)b.partials, nbin, b.acc);
+    if (e != cudaSuccess) return e;
+    switch (kp.P) {
+#define SE_CASE(PP) case PP: return fast_spread_P<PP>(kp, b, s);
+        SE_FOR_EACH_P(SE_CASE)
+#undef SE_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t fast_transform(const KParams<float>& kp, const FastBufs& b, double e_scale,
+                           double* E_grid, cudaStream_t s, bool marks, void (*mark)(void*, int),
+                           void* ctx) {
+    const int M = kp.M, Mh = M / 2 + 1;
+    const int nch = (Mh + kFastKC - 1) / kFastKC;
+    const float2* tw = (const float2*)b.tw;
+    float2* C = (float2*)b.cgrid;
+    const size_t slab = slab_smem_bytes(M);
+    cudaError_t e = cudaFuncSetAttribute(k_slab_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_slab_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab);
+    if (e != cudaSuccess) return e;
+    e = launch_ex(k_slab_fwd, M, kSlabThreads, slab, s, true, (const long long*)b.g64, C, tw, M,
+                  (const Acc*)b.acc);
+    if (e != cudaSuccess) return e;
+    if (marks) mark(ctx, 3);
+    const float invM3 = (float)(1.0 / ((double)M * M * M));
+    e = launch_ex(k_xpass, M * nch, kThreads, 0, s, true, C, tw, b.green_f, M, invM3,
+                  b.partials + 5 * kMaxPartials, b.tickets + 1, b.acc, e_scale, E_grid);
+    if (e != cudaSuccess) return e;
+    if (marks) mark(ctx, 4);
+    e = launch_ex(k_slab_inv, M, kSlabThreads, slab, s, true, (const float2*)C, b.rgrid, tw, M);
+    if (e != cudaSuccess) return e;
+    if (marks) mark(ctx, 5);
+    return cudaSuccess;
+}
+
+cudaError_t fast_to_real(const FastBufs& b, int M, float* dst, cudaStream_t s) {
+    const long long n = (long long)M * M * M;
+    const int blocks = (int)std::max(1LL, std::min((n + 255) / 256, 4096LL));
+    return launch_ex(k_fx_to_real, blocks, kThreads, 0, s, false, (const long long*)b.g64, dst, n,
+                     (const Acc*)b.acc);
+}
+
+template <int P>
+cudaError_t gather_pdl_P(const f4* sorted, const int* perm, const float* grid, float* phi,
+                         float* F, const KParams<float>& kp, double* partials, unsigned* ticket,
+                         Acc* acc, double e_scale, double* E_out, cudaStream_t s) {
+    constexpr int GPW = 32 / (P / pick_d(P));
+    const int gpb = (kThreads / 32) * GPW;
+    const int blocks = std::max(1, std::min((kp.N + gpb - 1) / gpb, kMaxPartials));
+    return launch_ex(k_gather<float, P>, blocks, kThreads, 0, s, true, sorted, perm, grid, phi, F,
+                     kp, partials, ticket, acc, e_scale, E_out);
+}
+
+cudaError_t launch_gather_pdl(const f4* sorted, const int* perm, const float* grid, float* phi,
+                              float* F, const KParams<float>& kp, double* partials,
+                              unsigned* ticket, Acc* acc, double e_scale, double* E_out,
+                              cudaStream_t s) {
+    switch (kp.P) {
+#define SE_CASE(PP) \
+    case PP: return gather_pdl_P<PP>(sorted, perm, grid, phi, F, kp, partials, ticket, acc, e_scale, E_out, s);
+        SE_FOR_EACH_P(SE_CASE)
+#undef SE_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace se
+
+#ifdef SE_TRACE
+// Copy the phase stamps of the traced kernels to the host (build with -DSE_TRACE).
+extern "C" int se_trace_read(unsigned long long* host, size_t bytes) {
+    if (bytes < sizeof(se::se_trace_buf)) return -1;
+    return cudaMemcpyFromSymbol(host, se::se_trace_buf, sizeof(se::se_trace_buf)) == cudaSuccess ? 0 : -2;
+}
+extern "C" int se_trace_clear(void) {
+    static unsigned long long zero[se::kTraceKernels][se::kTraceBlocks][se::kTracePhases];
+    return cudaMemcpyToSymbol(se::se_trace_buf, zero, sizeof(zero)) == cudaSuccess ? 0 : -2;
+}
+#endif

@@ -42,8 +42,9 @@ struct Acc {
     double e_grid;       // sum_k w_k G |H^_k|^2 over the half spectrum (scale)
     double e_gather;     // sum_m q_m phi_m, phi including the prefactor (gather)
     unsigned int nonfinite;  // number of particles with NaN/Inf position or charge (bin)
-    unsigned int pad0;
-    double pad[2];
+    int fx_shift;            // fixed-point spread: weights scaled by 2^fx_shift
+    float fx_scale, fx_inv;  // 2^fx_shift and 2^-fx_shift
+    double pad;
 };
 
 // launchers (se_kernels_*.cu)
@@ -73,7 +74,38 @@ cudaError_t launch_gather(const v4_t<T>* sorted, const int* perm, const T* grid,
 // Kernel parameters for an FP64 evaluation without a plan (se_plan.cu).
 int make_kparams_f64(int64_t N, double L, double xi, int M, int P, int tile, KParams<double>* out);
 
+// single-precision pipeline without cuFFT (se_fast.cuh)
+struct FastBufs {
+    long long* g64;       // M^3 fixed-point spread grid
+    void* cgrid;          // M x M x (M/2+1) float2
+    float* rgrid;         // M^3 real grid after the inverse transform
+    const void* tw;       // M twiddles (cos, sin)(2 pi r / M), float2
+    const double* green;  // G(k) on the half spectrum
+    const float* green_f; // the same table rounded to float
+    int* tile_count;
+    int* tile_start;
+    int* slot;
+    int* tile_of;
+    int* perm;
+    void* sorted;         // f4 [N]
+    double* partials;     // bin: [0, 3*1024); x pass: [5*1024, 7*1024)
+    unsigned* tickets;
+    Acc* acc;
+};
+cudaError_t fast_spread(const float* xyz, const float* q, const KParams<float>& kp,
+                        const FastBufs& b, cudaStream_t s);
+cudaError_t fast_transform(const KParams<float>& kp, const FastBufs& b, double e_scale,
+                           double* E_grid, cudaStream_t s, bool marks, void (*mark)(void*, int),
+                           void* ctx);
+cudaError_t fast_to_real(const FastBufs& b, int M, float* dst, cudaStream_t s);
+cudaError_t launch_gather_pdl(const f4* sorted, const int* perm, const float* grid, float* phi,
+                              float* F, const KParams<float>& kp, double* partials,
+                              unsigned* ticket, Acc* acc, double e_scale, double* E_out,
+                              cudaStream_t s);
+
 constexpr int kMaxPartials = 1024;   // blocks of the reducing kernels
+constexpr int kFastMaxM = 128;       // largest grid of the single-precision pipeline
+constexpr int kScanLimit = 8192;     // tiles scanned in shared memory
 constexpr size_t kSmemBudget = 200 * 1024;  // dynamic shared memory for a spreading tile
 
 }  // namespace se

@@ -27,6 +27,10 @@ __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, 
 __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ float expT(float a) { return expf(a); }
 __device__ __forceinline__ double expT(double a) { return exp(a); }
+// floor in the argument's own precision (a float must not go through the
+// FP64 pipe; the result is the same integer-valued number either way)
+__device__ __forceinline__ float floorT(float a) { return floorf(a); }
+__device__ __forceinline__ double floorT(double a) { return floor(a); }
 
 // Wrap one coordinate into [0, L): untouched when already inside, else
 // x - L floor(x / L) with the reciprocal rounded once; anything left outside
@@ -35,7 +39,7 @@ template <typename T>
 __device__ __forceinline__ T wrap_coord(T x, T L, T invL) {
     if (x >= T(0) && x < L) return x;
     T s = mul_rn(x, invL);
-    T f = floor(s);
+    T f = floorT(s);
     T p = mul_rn(f, L);
     T w = sub_rn(x, p);
     if (w >= L) w = sub_rn(w, L);
@@ -49,7 +53,7 @@ template <typename T>
 __device__ __forceinline__ int cell_of(T xw, T invh, int M, T* t) {
     T s = mul_rn(xw, invh);
     *t = s;
-    int c = (int)floor(s);
+    int c = (int)floorT(s);
     return c >= M ? M - 1 : (c < 0 ? 0 : c);
 }
 
@@ -79,6 +83,32 @@ __device__ __forceinline__ void fgg(T u, T beta, const T (&E3)[kMaxP], T (&g)[P]
         p *= B;
     }
 }
+
+// Programmatic dependent launch: wait for the preceding kernel's results
+// (a no-op when the kernel was launched without the attribute), and let the
+// next kernel be scheduled early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_next() { asm volatile("griddepcontrol.launch_dependents;"); }
+
+// Optional phase tracing (build with -DSE_TRACE): thread 0 of each block
+// records %globaltimer at phase boundaries of the single-precision kernels
+// into se_trace_buf[kernel][block][phase]; compiled out otherwise.
+#ifdef SE_TRACE
+constexpr int kTraceKernels = 8, kTraceBlocks = 2048, kTracePhases = 8;
+__device__ unsigned long long se_trace_buf[kTraceKernels][kTraceBlocks][kTracePhases];
+#define SE_STAMP(kid, ph)                                                                   \
+    do {                                                                                    \
+        if (threadIdx.x == 0 && blockIdx.x < kTraceBlocks) {                                \
+            unsigned long long t_;                                                          \
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_));                          \
+            se_trace_buf[kid][blockIdx.x][ph] = t_;                                         \
+        }                                                                                   \
+    } while (0)
+#else
+#define SE_STAMP(kid, ph) \
+    do {                  \
+    } while (0)
+#endif
 
 // Lanes per particle: a particle's P z-points are split over G = P / D lanes
 // (D points each); D is the smallest divisor of P that keeps >= 85% of the
@@ -112,6 +142,57 @@ __device__ __forceinline__ double block_sum(double v, double* sbuf) {
     if (threadIdx.x == 0)
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sbuf[w];
     return r;  // valid in thread 0
+}
+
+// ---------------------------------------------------------------------------
+// Double-float sums: a value hi + lo held in two floats (about 48 significant
+// bits), added with two-sum.  The single-precision kernels reduce energies and
+// charge sums this way: a chain of dependent FP64 additions costs microseconds
+// on this GPU, FP32 two-sums do not.
+struct df2 {
+    float hi, lo;
+};
+__device__ __forceinline__ df2 df_add(df2 a, df2 b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bp = __fsub_rn(s, a.hi);
+    const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bp)), __fsub_rn(b.hi, bp));
+    const float lo = __fadd_rn(__fadd_rn(a.lo, b.lo), err);
+    const float hi = __fadd_rn(s, lo);
+    return df2{hi, __fsub_rn(lo, __fsub_rn(hi, s))};
+}
+__device__ __forceinline__ df2 df_from(float v) { return df2{v, 0.0f}; }
+__device__ __forceinline__ double df_to_double(df2 a) { return (double)a.hi + (double)a.lo; }
+
+// Block-wide double-float sum (blockDim.x a multiple of 32); valid in thread 0.
+__device__ __forceinline__ df2 block_sum_df(df2 v, df2* sbuf) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        df2 u;
+        u.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        u.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        v = df_add(v, u);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sbuf[warp] = v;
+    __syncthreads();
+    df2 r = df_from(0.0f);
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = df_add(r, sbuf[w]);
+    return r;
+}
+
+// Sum of n double-float partials (pairs of floats, stride apart, from offset).
+__device__ __forceinline__ df2 sum_partials_df(const float* partials, int n, int stride,
+                                               int offset, df2* sbuf) {
+    df2 v = df_from(0.0f);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        df2 u;
+        u.hi = __ldcg(partials + 2 * (k * stride + offset));
+        u.lo = __ldcg(partials + 2 * (k * stride + offset) + 1);
+        v = df_add(v, u);
+    }
+    return block_sum_df(v, sbuf);
 }
 
 // Last-block detection: every block stores its partial, fences, and takes a
@@ -486,7 +567,12 @@ k_gather(const v4_t<T>* __restrict__ sorted, const int* __restrict__ perm,
          const KParams<T> kp, double* __restrict__ partials, unsigned* ticket, Acc* acc,
          double e_scale, double* E_out) {
     constexpr int D = pick_d(P), G = P / D, GPW = 32 / G;
+    constexpr bool kSingle = sizeof(T) == sizeof(float);
+    SE_STAMP(6, 0);
+    pdl_wait();
+    SE_STAMP(6, 1);
     __shared__ double sbuf[32];
+    __shared__ df2 sbuf_df[32];
     __shared__ T sE3[P];
     if (threadIdx.x < P) sE3[threadIdx.x] = kp.E3[threadIdx.x];
     __syncthreads();
@@ -495,6 +581,7 @@ k_gather(const v4_t<T>* __restrict__ sorted, const int* __restrict__ perm,
     const int gpb = (blockDim.x >> 5) * GPW;
     const int M = kp.M;
     double e_loc = 0.0;
+    df2 e_df = df_from(0.0f);
     for (int pb = blockIdx.x * gpb + warp * GPW; pb < kp.N; pb += gridDim.x * gpb) {
         const int p = pb + gi;
         const bool valid = (gi < GPW) && (p < kp.N);
@@ -533,7 +620,9 @@ k_gather(const v4_t<T>* __restrict__ sorted, const int* __restrict__ perm,
             for (int j = 0; j < D; ++j) acc0[j] = accx[j] = accy[j] = T(0);
             const T Bx = expT(T(2) * kp.beta * ux);
             T px = expT(-kp.beta * ux * (ux + T(P - 1)));
-#pragma unroll 1
+            // small supports: the whole x loop unrolled, so that every load of
+            // the particle's P^3 grid values is in flight at once
+#pragma unroll(P <= 8 ? P : 1)
             for (int a = 0; a < P; ++a) {
                 const T gxa = px * sE3[a];
                 const T dgxa = (T(a) - T(0.5) * T(P - 1) - ux) * gxa;
@@ -567,6 +656,7 @@ k_gather(const v4_t<T>* __restrict__ sorted, const int* __restrict__ perm,
                 vfz += dgz[j] * acc0[j];
             }
         }
+        SE_STAMP(6, 2);
         // reduce over the G lanes of each particle (lane 0 of the group ends with the sum)
 #pragma unroll
         for (int o = 1; o < G; o <<= 1) {
@@ -591,8 +681,34 @@ k_gather(const v4_t<T>* __restrict__ sorted, const int* __restrict__ perm,
                 F[3 * orig + 1] = fs * vfy;
                 F[3 * orig + 2] = fs * vfz;
             }
-            e_loc += (double)qq * (double)ph;
+            if (kSingle)
+                e_df = df_add(e_df, df_from((float)(qq * ph)));
+            else
+                e_loc += (double)qq * (double)ph;
         }
+    }
+    SE_STAMP(6, 3);
+    if (kSingle) {
+        // double-float partials: (hi, lo) floats per block
+        float* pf = reinterpret_cast<float*>(partials);
+        const df2 r = block_sum_df(e_df, sbuf_df);
+        SE_STAMP(6, 4);
+        if (threadIdx.x == 0) {
+            pf[2 * blockIdx.x] = r.hi;
+            pf[2 * blockIdx.x + 1] = r.lo;
+        }
+        const bool lastb = last_block(ticket);
+        SE_STAMP(6, 5);
+        if (!lastb) return;
+        const df2 t = sum_partials_df(pf, gridDim.x, 1, 0, sbuf_df);
+        SE_STAMP(6, 6);
+        if (threadIdx.x == 0) {
+            const double s = df_to_double(t);
+            acc->e_gather = s;
+            if (E_out) *E_out = e_scale * s;
+            *ticket = 0u;
+        }
+        return;
     }
     double r = block_sum(e_loc, sbuf);
     if (threadIdx.x == 0) partials[blockIdx.x] = r;

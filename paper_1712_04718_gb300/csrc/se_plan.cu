@@ -55,7 +55,10 @@ struct se_plan {
     int* tile_of = nullptr;
     int* perm = nullptr;
     void* sorted = nullptr;
-    double* partials = nullptr;    // 5 x kMaxPartials
+    long long* g64 = nullptr;      // fixed-point spread grid (single-precision pipeline)
+    float* green_f = nullptr;      // G(k) table in float (single-precision pipeline)
+    void* tw = nullptr;            // twiddles of the single-precision pipeline
+    double* partials = nullptr;    // 8 x kMaxPartials
     unsigned* tickets = nullptr;   // bin, scale, gather
     Acc* acc = nullptr;
     double* dE = nullptr;          // device energy for se_energy_force
@@ -152,15 +155,20 @@ void derive(se_plan* p) {
     p->alpha = 2.0 * p->xi * p->xi / p->eta;
     p->cg = pow(2.0 * p->xi * p->xi / (kPi * p->eta), 1.5);
     // spreading variant and tile edge
-    int variant = p->tune_variant;
-    if (variant == 0) variant = (p->prec == SE_FP64 && p->P > 12) ? 2 : 1;
-    if (p->prec == SE_FP32) variant = 1;  // the compensated sum needs the tiles
-    p->variant = variant;
     int tile = p->tune_tile > 0 ? p->tune_tile : 8;
     if (tile > p->M) tile = p->M;
     p->tile = tile;
     p->nT = (p->M + tile - 1) / tile;
     p->ntiles = p->nT * p->nT * p->nT;
+    const bool fast_ok = p->prec != SE_FP64 && p->M <= se::kFastMaxM && p->ntiles <= se::kScanLimit;
+    int variant = p->tune_variant;
+    if (variant == 3 && !fast_ok) variant = 0;
+    if (variant == 0) {
+        if (p->prec == SE_FP64) variant = p->P > 12 ? 2 : 1;
+        else variant = fast_ok ? 3 : 1;
+    }
+    if (p->prec == SE_FP32 && variant == 2) variant = 1;  // the compensated sum needs the tiles
+    p->variant = variant;
 }
 
 void drop_graph(se_plan* p) {
@@ -177,10 +185,12 @@ void release_device(se_plan* p) {
     }
     void* bufs[] = {p->grid_spread, p->grid_gather, p->cgrid, p->green, p->tile_count,
                     p->tile_start, p->slot, p->tile_of, p->perm, p->sorted, p->partials,
-                    p->tickets, p->acc, p->dE, p->h_xyz, p->h_q, p->h_F, p->h_phi};
+                    p->tickets, p->acc, p->dE, p->h_xyz, p->h_q, p->h_F, p->h_phi, p->g64, p->tw, p->green_f};
     for (void* b : bufs)
         if (b) cudaFree(b);
-    p->grid_spread = p->grid_gather = p->cgrid = p->sorted = nullptr;
+    p->grid_spread = p->grid_gather = p->cgrid = p->sorted = p->tw = nullptr;
+    p->g64 = nullptr;
+    p->green_f = nullptr;
     p->green = p->partials = p->dE = nullptr;
     p->tile_count = p->tile_start = p->slot = p->tile_of = p->perm = nullptr;
     p->tickets = nullptr;
@@ -255,8 +265,12 @@ int prepare(se_plan* p) {
     const size_t M3 = (size_t)p->M * p->M * p->M;
     const size_t nc = (size_t)p->M * p->M * (p->M / 2 + 1);
     const size_t N = (size_t)p->N;
+    const bool fast = p->variant == 3;
     int rc = SE_OK;
-    if (rc == SE_OK) rc = dalloc(&p->grid_spread, M3 * ts);
+    if (rc == SE_OK && !fast) rc = dalloc(&p->grid_spread, M3 * ts);
+    if (rc == SE_OK && fast) rc = dalloc((void**)&p->g64, M3 * sizeof(long long));
+    if (rc == SE_OK && fast) rc = dalloc(&p->tw, (size_t)p->M * 2 * sizeof(float));
+    if (rc == SE_OK && fast) rc = dalloc((void**)&p->green_f, nc * sizeof(float));
     if (rc == SE_OK) rc = dalloc(&p->grid_gather, M3 * ts);
     if (rc == SE_OK) rc = dalloc(&p->cgrid, nc * 2 * ts);
     if (rc == SE_OK) rc = dalloc((void**)&p->green, nc * sizeof(double));
@@ -266,7 +280,7 @@ int prepare(se_plan* p) {
     if (rc == SE_OK) rc = dalloc((void**)&p->tile_of, N * sizeof(int));
     if (rc == SE_OK) rc = dalloc((void**)&p->perm, N * sizeof(int));
     if (rc == SE_OK) rc = dalloc(&p->sorted, N * 4 * ts);
-    if (rc == SE_OK) rc = dalloc((void**)&p->partials, 5 * se::kMaxPartials * sizeof(double));
+    if (rc == SE_OK) rc = dalloc((void**)&p->partials, 8 * se::kMaxPartials * sizeof(double));
     if (rc == SE_OK) rc = dalloc((void**)&p->tickets, 4 * sizeof(unsigned));
     if (rc == SE_OK) rc = dalloc((void**)&p->acc, sizeof(Acc));
     if (rc == SE_OK) rc = dalloc((void**)&p->dE, sizeof(double));
@@ -279,9 +293,37 @@ int prepare(se_plan* p) {
         cudaMemset(p->tile_count, 0, (size_t)p->ntiles * sizeof(int)) != cudaSuccess ||
         cudaMemset(p->tickets, 0, 4 * sizeof(unsigned)) != cudaSuccess ||
         cudaMemset(p->acc, 0, sizeof(Acc)) != cudaSuccess ||
-        cudaMemset(p->grid_spread, 0, M3 * ts) != cudaSuccess) {
+        (!fast && cudaMemset(p->grid_spread, 0, M3 * ts) != cudaSuccess)) {
         release_device(p);
         return SE_ERR_CUDA;
+    }
+    if (fast) {
+        // twiddles (cos, sin)(2 pi r / M), exact at the quarter turns
+        std::vector<float> tw(2 * (size_t)p->M);
+        for (int r = 0; r < p->M; ++r) {
+            double c = cos(2.0 * kPi * r / p->M), sn = sin(2.0 * kPi * r / p->M);
+            if ((4 * r) % p->M == 0) {
+                const int q4 = (4 * r) / p->M;
+                c = q4 == 0 ? 1.0 : (q4 == 2 ? -1.0 : 0.0);
+                sn = q4 == 1 ? 1.0 : (q4 == 3 ? -1.0 : 0.0);
+            }
+            tw[2 * r] = (float)c;
+            tw[2 * r + 1] = (float)sn;
+        }
+        std::vector<float> gf(nc);
+        for (size_t i = 0; i < nc; ++i) gf[i] = (float)g[i];
+        if (cudaMemcpy(p->tw, tw.data(), tw.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(p->green_f, gf.data(), nc * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+            release_device(p);
+            return SE_ERR_CUDA;
+        }
+    }
+    if (fast) {
+        p->spread_clean = true;
+        p->have_spread = p->have_scale = false;
+        p->ready = true;
+        p->ready_prec = p->prec;
+        return SE_OK;
     }
     const cufftType tf = p->prec == SE_FP64 ? CUFFT_D2Z : CUFFT_R2C;
     const cufftType ti = p->prec == SE_FP64 ? CUFFT_Z2D : CUFFT_C2R;
@@ -306,6 +348,59 @@ void invalidate(se_plan* p) {
     // parameters changed: rebuild tables and buffers at the next call
     if (p->ready) release_device(p);
     derive(p);
+}
+
+se::FastBufs fast_bufs(se_plan* p) {
+    se::FastBufs b;
+    b.g64 = p->g64;
+    b.cgrid = p->cgrid;
+    b.rgrid = (float*)p->grid_gather;
+    b.tw = p->tw;
+    b.green = p->green;
+    b.green_f = p->green_f;
+    b.tile_count = p->tile_count;
+    b.tile_start = p->tile_start;
+    b.slot = p->slot;
+    b.tile_of = p->tile_of;
+    b.perm = p->perm;
+    b.sorted = p->sorted;
+    b.partials = p->partials;
+    b.tickets = p->tickets;
+    b.acc = p->acc;
+    return b;
+}
+
+void mark_cb(void* ctx, int s) { timing_mark(static_cast<se_plan*>(ctx), s); }
+
+int fast_spread(se_plan* p, const void* xyz, const void* q) {
+    const KParams<float> kp = make_kparams<float>(p);
+    timing_begin(p);
+    SE_CUDA(se::fast_spread((const float*)xyz, (const float*)q, kp, fast_bufs(p), p->stream));
+    timing_mark(p, 0);
+    timing_mark(p, 1);
+    timing_mark(p, 2);
+    p->have_spread = true;
+    p->have_scale = false;
+    return SE_OK;
+}
+
+int fast_scale(se_plan* p, double* E_grid) {
+    const KParams<float> kp = make_kparams<float>(p);
+    const double M3 = (double)p->M * p->M * p->M;
+    const double e_scale = p->kc * p->h * p->h * p->h / (2.0 * M3);
+    SE_CUDA(se::fast_transform(kp, fast_bufs(p), e_scale, E_grid, p->stream, p->ev_cur >= 0,
+                               mark_cb, p));
+    p->have_scale = true;
+    return SE_OK;
+}
+
+int fast_gather(se_plan* p, void* phi, void* F, double* E) {
+    const KParams<float> kp = make_kparams<float>(p);
+    SE_CUDA(se::launch_gather_pdl((const se::f4*)p->sorted, p->perm, (const float*)p->grid_gather,
+                                  (float*)phi, (float*)F, kp, p->partials + 4 * se::kMaxPartials,
+                                  p->tickets + 2, p->acc, 0.5, E, p->stream));
+    timing_mark(p, 6);
+    return SE_OK;
 }
 
 template <typename T>
@@ -377,6 +472,12 @@ int status_from_acc(const Acc& a) {
 }
 
 int evaluate(se_plan* p, const void* xyz, const void* q, void* F, void* phi, double* dE) {
+    if (p->variant == 3) {
+        SE_TRY(fast_spread(p, xyz, q));
+        SE_TRY(fast_scale(p, nullptr));
+        SE_TRY(fast_gather(p, phi, F, dE));
+        return SE_OK;
+    }
     if (p->prec == SE_FP64) {
         SE_TRY(do_spread<double>(p, xyz, q));
         SE_TRY(do_scale<double>(p, nullptr));
@@ -404,7 +505,7 @@ int graph_evaluate(se_plan* p, const void* xyz, const void* q, void* F, void* ph
         drop_graph(p);
         if (!p->cap_stream)
             SE_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
-        if (!p->spread_clean) {
+        if (!p->spread_clean && p->variant != 3) {
             const size_t M3 = (size_t)p->M * p->M * p->M;
             SE_CUDA(cudaMemsetAsync(p->grid_spread, 0, M3 * tsize(p->prec), p->stream));
             p->spread_clean = true;
@@ -568,8 +669,9 @@ int se_plan_set_stream(se_plan* p, void* stream) {
 }
 
 int se_plan_set_tuning(se_plan* p, int spread_variant, int tile) {
-    if (!p || spread_variant < 0 || spread_variant > 2 || (tile != 0 && (tile < 2 || tile > 32)))
+    if (!p || spread_variant < 0 || spread_variant > 3 || (tile != 0 && (tile < 2 || tile > 32)))
         return SE_ERR_ARG;
+    if (spread_variant == 3 && (p->prec == SE_FP64 || p->M > se::kFastMaxM)) return SE_ERR_UNSUPPORTED;
     if (spread_variant == 2 && p->prec == SE_FP32) return SE_ERR_UNSUPPORTED;
     p->tune_variant = spread_variant;
     p->tune_tile = tile;
@@ -595,18 +697,21 @@ int se_plan_get_params(const se_plan* p, double* out) {
 int se_spread(se_plan* p, const void* xyz, const void* q) {
     if (!p || (p->N > 0 && (!xyz || !q))) return SE_ERR_ARG;
     SE_TRY(prepare(p));
+    if (p->variant == 3) return fast_spread(p, xyz, q);
     return p->prec == SE_FP64 ? do_spread<double>(p, xyz, q) : do_spread<float>(p, xyz, q);
 }
 
 int se_scale(se_plan* p, double* E_grid) {
     if (!p) return SE_ERR_ARG;
     if (!p->ready || !p->have_spread) return SE_ERR_ARG;
+    if (p->variant == 3) return fast_scale(p, E_grid);
     return p->prec == SE_FP64 ? do_scale<double>(p, E_grid) : do_scale<float>(p, E_grid);
 }
 
 int se_gather(se_plan* p, const void* xyz, const void* q, void* phi, void* F, double* E) {
     if (!p || (p->N > 0 && (!xyz || !q))) return SE_ERR_ARG;
     if (!p->ready || !p->have_scale) return SE_ERR_ARG;
+    if (p->variant == 3) return fast_gather(p, phi, F, E);
     return p->prec == SE_FP64 ? do_gather<double>(p, phi, F, E) : do_gather<float>(p, phi, F, E);
 }
 
@@ -680,6 +785,8 @@ int se_copy_grid(se_plan* p, int which, void* dst) {
     if (!p || !dst || (which != 0 && which != 1)) return SE_ERR_ARG;
     if (!p->ready) return SE_ERR_ARG;
     const size_t bytes = (size_t)p->M * p->M * p->M * tsize(p->prec);
+    if (which == 0 && p->variant == 3)
+        return check_cuda(se::fast_to_real(fast_bufs(p), p->M, (float*)dst, p->stream));
     SE_CUDA(cudaMemcpyAsync(dst, which == 0 ? p->grid_spread : p->grid_gather, bytes,
                             cudaMemcpyDeviceToDevice, p->stream));
     return SE_OK;

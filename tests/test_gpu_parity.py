@@ -75,9 +75,11 @@ def oracle_for(x, q, L, xi, M, P, prec, grids=False):
                             L, xi, M, P, cell_mode=cm, grids=grids)
 
 
-SMALL = [  # (M, P, tile, variant): ragged tiles, P = M, large support, small tiles
+SMALL = [  # (M, P, tile, variant): ragged tiles, P = M, large support, small tiles;
+    # variant 0 = automatic (the single-precision pipeline for FP32), 1 = tiles + cuFFT
     (20, 8, 8, 0), (16, 4, 8, 0), (18, 10, 8, 0), (24, 12, 4, 0), (12, 12, 8, 0),
-    (32, 16, 8, 0), (10, 2, 4, 0), (28, 6, 5, 0),
+    (32, 16, 8, 0), (10, 2, 4, 0), (28, 6, 5, 0), (25, 8, 8, 0), (21, 6, 8, 0),
+    (20, 8, 8, 1), (28, 6, 5, 1), (25, 8, 8, 1),
 ]
 
 
