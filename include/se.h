@@ -128,6 +128,16 @@ int se_scale(se_plan *plan, double *E_grid);
 int se_gather(se_plan *plan, const void *xyz, const void *q, void *phi, void *F,
               double *E);
 
+/* Adjoint of the energy (the backward step of E^L as a differentiable
+ * function of positions and charges): with the upstream gradient
+ * g = dl/dE^L (DEVICE pointer to one double), writes
+ *   grad_x = dl/dx = -g F     (F = -dE/dx, Sec. 1 Eq. 1.3)
+ *   grad_q = dl/dq = g phi    (E is quadratic in q and 1/2 sum q phi, Eq. 1.2)
+ * into DEVICE arrays of the plan's type ([N][3] and [N]; each may be NULL).
+ * Reuses the grid of the last se_scale (same xyz, q); no host sync. */
+int se_adjoint(se_plan *plan, const void *xyz, const void *q, const double *gE,
+               void *grad_x, void *grad_q);
+
 /* The whole k-space evaluation: se_spread, se_scale, se_gather.  E is a HOST
  * pointer (the call waits for the stream); F and phi are device pointers and
  * may be NULL.  Returns SE_WARN_NONNEUTRAL for a non-neutral system and

@@ -39,6 +39,7 @@ SIGNATURES = {
     "se_scale": (_i, [_vp, _vp]),
     "se_gather": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "se_energy_force": (_i, [_vp, _vp, _vp, _dp, _vp, _vp]),
+    "se_adjoint": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "se_energy_force_host": (_i, [_vp, _vp, _vp, _dp, _vp, _vp]),
     "se_copy_grid": (_i, [_vp, _i, _vp]),
     "se_self_energy": (_i, [_vp, _vp, _i64, _dp]),

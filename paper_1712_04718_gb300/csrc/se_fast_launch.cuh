@@ -102,21 +102,22 @@ cudaError_t fast_to_real(const FastBufs& b, int M, float* dst, cudaStream_t s) {
 template <int P>
 cudaError_t gather_pdl_P(const f4* sorted, const int* perm, const float* grid, float* phi,
                          float* F, const KParams<float>& kp, double* partials, unsigned* ticket,
-                         Acc* acc, double e_scale, double* E_out, cudaStream_t s) {
+                         Acc* acc, double e_scale, double* E_out, const double* adj,
+                         cudaStream_t s) {
     constexpr int GPW = 32 / (P / pick_d(P));
     const int gpb = (kThreads / 32) * GPW;
     const int blocks = std::max(1, std::min((kp.N + gpb - 1) / gpb, kMaxPartials));
     return launch_ex(k_gather<float, P>, blocks, kThreads, 0, s, true, sorted, perm, grid, phi, F,
-                     kp, partials, ticket, acc, e_scale, E_out);
+                     kp, partials, ticket, acc, e_scale, E_out, adj);
 }
 
 cudaError_t launch_gather_pdl(const f4* sorted, const int* perm, const float* grid, float* phi,
                               float* F, const KParams<float>& kp, double* partials,
                               unsigned* ticket, Acc* acc, double e_scale, double* E_out,
-                              cudaStream_t s) {
+                              const double* adj, cudaStream_t s) {
     switch (kp.P) {
 #define SE_CASE(PP) \
-    case PP: return gather_pdl_P<PP>(sorted, perm, grid, phi, F, kp, partials, ticket, acc, e_scale, E_out, s);
+    case PP: return gather_pdl_P<PP>(sorted, perm, grid, phi, F, kp, partials, ticket, acc, e_scale, E_out, adj, s);
         SE_FOR_EACH_P(SE_CASE)
 #undef SE_CASE
         default: return cudaErrorInvalidValue;

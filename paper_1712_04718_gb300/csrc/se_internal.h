@@ -69,7 +69,8 @@ cudaError_t launch_scale(void* cgrid, const double* green, int M, T* zero_grid,
 template <typename T>
 cudaError_t launch_gather(const v4_t<T>* sorted, const int* perm, const T* grid, T* phi,
                           T* F, const KParams<T>& kp, double* partials, unsigned* ticket,
-                          Acc* acc, double e_scale, double* E_out, cudaStream_t s);
+                          Acc* acc, double e_scale, double* E_out, const double* adj,
+                          cudaStream_t s);
 
 // Kernel parameters for an FP64 evaluation without a plan (se_plan.cu).
 int make_kparams_f64(int64_t N, double L, double xi, int M, int P, int tile, KParams<double>* out);
@@ -101,7 +102,7 @@ cudaError_t fast_to_real(const FastBufs& b, int M, float* dst, cudaStream_t s);
 cudaError_t launch_gather_pdl(const f4* sorted, const int* perm, const float* grid, float* phi,
                               float* F, const KParams<float>& kp, double* partials,
                               unsigned* ticket, Acc* acc, double e_scale, double* E_out,
-                              cudaStream_t s);
+                              const double* adj, cudaStream_t s);
 
 constexpr int kMaxPartials = 1024;   // blocks of the reducing kernels
 constexpr int kFastMaxM = 128;       // largest grid of the single-precision pipeline

@@ -565,7 +565,7 @@ __global__ void __launch_bounds__(256)
 k_gather(const v4_t<T>* __restrict__ sorted, const int* __restrict__ perm,
          const T* __restrict__ grid, T* __restrict__ phi, T* __restrict__ F,
          const KParams<T> kp, double* __restrict__ partials, unsigned* ticket, Acc* acc,
-         double e_scale, double* E_out) {
+         double e_scale, double* E_out, const double* __restrict__ adj) {
     constexpr int D = pick_d(P), G = P / D, GPW = 32 / G;
     constexpr bool kSingle = sizeof(T) == sizeof(float);
     SE_STAMP(6, 0);
@@ -580,6 +580,10 @@ k_gather(const v4_t<T>* __restrict__ sorted, const int* __restrict__ perm,
     const int gi = lane / G, k = lane - gi * G;
     const int gpb = (blockDim.x >> 5) * GPW;
     const int M = kp.M;
+    // adjoint (backward) mode: outputs are dl/dq = g phi and dl/dx = -g F for
+    // the upstream gradient g = dl/dE read from device memory
+    const T gsc = adj ? (T)__ldg(adj) : T(1);
+    const T phi_mul = gsc, F_mul = adj ? -gsc : T(1);
     double e_loc = 0.0;
     df2 e_df = df_from(0.0f);
     for (int pb = blockIdx.x * gpb + warp * GPW; pb < kp.N; pb += gridDim.x * gpb) {
@@ -675,11 +679,12 @@ k_gather(const v4_t<T>* __restrict__ sorted, const int* __restrict__ perm,
             const T ph = vphi * kp.phi_scale;
             const T fs = qq * kp.F_scale;
             const int orig = perm[p];
-            if (phi) phi[orig] = ph;
+            if (phi) phi[orig] = ph * phi_mul;
             if (F) {
-                F[3 * orig] = fs * vfx;
-                F[3 * orig + 1] = fs * vfy;
-                F[3 * orig + 2] = fs * vfz;
+                const T fm = fs * F_mul;
+                F[3 * orig] = fm * vfx;
+                F[3 * orig + 1] = fm * vfy;
+                F[3 * orig + 2] = fm * vfz;
             }
             if (kSingle)
                 e_df = df_add(e_df, df_from((float)(qq * ph)));

@@ -102,22 +102,23 @@ cudaError_t launch_scale(void* cgrid, const double* green, int M, T* zero_grid,
 template <typename T, int P>
 cudaError_t gather_P(const v4_t<T>* sorted, const int* perm, const T* grid, T* phi, T* F,
                      const KParams<T>& kp, double* partials, unsigned* ticket, Acc* acc,
-                     double e_scale, double* E_out, cudaStream_t s) {
+                     double e_scale, double* E_out, const double* adj, cudaStream_t s) {
     constexpr int GPW = 32 / (P / pick_d(P));
     const int gpb = (kThreads / 32) * GPW;
     const int blocks = std::max(1, std::min((kp.N + gpb - 1) / gpb, kMaxPartials));
     k_gather<T, P><<<blocks, kThreads, 0, s>>>(sorted, perm, grid, phi, F, kp, partials, ticket,
-                                               acc, e_scale, E_out);
+                                               acc, e_scale, E_out, adj);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_gather(const v4_t<T>* sorted, const int* perm, const T* grid, T* phi,
                           T* F, const KParams<T>& kp, double* partials, unsigned* ticket,
-                          Acc* acc, double e_scale, double* E_out, cudaStream_t s) {
+                          Acc* acc, double e_scale, double* E_out, const double* adj,
+                          cudaStream_t s) {
     switch (kp.P) {
 #define SE_CASE(PP) \
-    case PP: return gather_P<T, PP>(sorted, perm, grid, phi, F, kp, partials, ticket, acc, e_scale, E_out, s);
+    case PP: return gather_P<T, PP>(sorted, perm, grid, phi, F, kp, partials, ticket, acc, e_scale, E_out, adj, s);
         SE_FOR_EACH_P(SE_CASE)
 #undef SE_CASE
         default: return cudaErrorInvalidValue;
@@ -137,6 +138,6 @@ cudaError_t launch_gather(const v4_t<T>* sorted, const int* perm, const T* grid,
                                          Acc*, double, double*, cudaStream_t);                  \
     template cudaError_t launch_gather<T>(const v4_t<T>*, const int*, const T*, T*, T*,         \
                                           const KParams<T>&, double*, unsigned*, Acc*, double,  \
-                                          double*, cudaStream_t);
+                                          double*, const double*, cudaStream_t);
 
 }  // namespace se

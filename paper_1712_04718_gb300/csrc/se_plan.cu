@@ -394,11 +394,11 @@ int fast_scale(se_plan* p, double* E_grid) {
     return SE_OK;
 }
 
-int fast_gather(se_plan* p, void* phi, void* F, double* E) {
+int fast_gather(se_plan* p, void* phi, void* F, double* E, const double* adj = nullptr) {
     const KParams<float> kp = make_kparams<float>(p);
     SE_CUDA(se::launch_gather_pdl((const se::f4*)p->sorted, p->perm, (const float*)p->grid_gather,
                                   (float*)phi, (float*)F, kp, p->partials + 4 * se::kMaxPartials,
-                                  p->tickets + 2, p->acc, 0.5, E, p->stream));
+                                  p->tickets + 2, p->acc, 0.5, E, adj, p->stream));
     timing_mark(p, 6);
     return SE_OK;
 }
@@ -455,12 +455,12 @@ int do_scale(se_plan* p, double* E_grid) {
 }
 
 template <typename T>
-int do_gather(se_plan* p, void* phi, void* F, double* E) {
+int do_gather(se_plan* p, void* phi, void* F, double* E, const double* adj = nullptr) {
     const KParams<T> kp = make_kparams<T>(p);
     using V = se::v4_t<T>;
     SE_CUDA(se::launch_gather<T>((const V*)p->sorted, p->perm, (const T*)p->grid_gather, (T*)phi,
                                  (T*)F, kp, p->partials + 4 * se::kMaxPartials, p->tickets + 2,
-                                 p->acc, 0.5, E, p->stream));
+                                 p->acc, 0.5, E, adj, p->stream));
     timing_mark(p, 6);
     return SE_OK;
 }
@@ -713,6 +713,15 @@ int se_gather(se_plan* p, const void* xyz, const void* q, void* phi, void* F, do
     if (!p->ready || !p->have_scale) return SE_ERR_ARG;
     if (p->variant == 3) return fast_gather(p, phi, F, E);
     return p->prec == SE_FP64 ? do_gather<double>(p, phi, F, E) : do_gather<float>(p, phi, F, E);
+}
+
+int se_adjoint(se_plan* p, const void* xyz, const void* q, const double* gE, void* grad_x,
+               void* grad_q) {
+    if (!p || !gE || (p->N > 0 && (!xyz || !q))) return SE_ERR_ARG;
+    if (!p->ready || !p->have_scale) return SE_ERR_ARG;
+    if (p->variant == 3) return fast_gather(p, grad_q, grad_x, nullptr, gE);
+    return p->prec == SE_FP64 ? do_gather<double>(p, grad_q, grad_x, nullptr, gE)
+                              : do_gather<float>(p, grad_q, grad_x, nullptr, gE);
 }
 
 int se_energy_force(se_plan* p, const void* xyz, const void* q, double* E, void* F, void* phi) {

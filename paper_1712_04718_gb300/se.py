@@ -50,6 +50,10 @@ class Plan:
             nat.check(self._lib.se_plan_set_tuning(self._h, int(spread_variant), int(tile)),
                       "se_plan_set_tuning")
         self.last_status = 0
+        # counts evaluations that overwrite the plan's grids (spreads); the
+        # autograd layer uses it to know whether the grid of a forward pass
+        # is still in place at its backward pass
+        self.generation = 0
 
     # -- bookkeeping -------------------------------------------------------
     @property
@@ -96,6 +100,7 @@ class Plan:
     def spread(self, xyz, q):
         self._check_inputs(xyz, q)
         self._stream()
+        self.generation += 1
         nat.check(self._lib.se_spread(self._h, _ptr(xyz), _ptr(q)), "se_spread")
 
     def scale(self, E_grid=None):
@@ -118,6 +123,7 @@ class Plan:
         if phi is None and with_phi:
             phi = torch.empty((self.N,), dtype=self.dtype, device=xyz.device)
         self._stream()
+        self.generation += 1
         E = ctypes.c_double()
         st = self._lib.se_energy_force(self._h, _ptr(xyz), _ptr(q), ctypes.byref(E), _ptr(F),
                                        _ptr(phi))
@@ -131,6 +137,7 @@ class Plan:
         F = np.empty((self.N, 3), dtype=self.np_dtype)
         phi = np.empty((self.N,), dtype=self.np_dtype)
         self._stream()
+        self.generation += 1
         E = ctypes.c_double()
         st = self._lib.se_energy_force_host(
             self._h, xyz.ctypes.data_as(ctypes.c_void_p), q.ctypes.data_as(ctypes.c_void_p),
@@ -142,6 +149,7 @@ class Plan:
     def energy_force_host_ptrs(self, xyz_ptr, q_ptr, F_ptr, phi_ptr):
         """se_energy_force_host on raw host pointers (e.g. pinned torch tensors)."""
         self._stream()
+        self.generation += 1
         E = ctypes.c_double()
         st = self._lib.se_energy_force_host(self._h, ctypes.c_void_p(xyz_ptr),
                                             ctypes.c_void_p(q_ptr), ctypes.byref(E),
@@ -167,8 +175,16 @@ class Plan:
         host synchronisation (E: optional CUDA float64 tensor of one element).
         Arguments are not re-checked here (hot path)."""
         self._stream()
+        self.generation += 1
         nat.check(self._lib.se_evaluate(self._h, _ptr(xyz), _ptr(q), _ptr(F), _ptr(phi), _ptr(E)),
                   "se_evaluate")
+
+    def adjoint(self, xyz, q, gE, grad_x=None, grad_q=None):
+        """se_adjoint: grad_x = -g F, grad_q = g phi for g = gE (CUDA float64, one
+        element), from the grid of the last scale() of this plan."""
+        self._stream()
+        nat.check(self._lib.se_adjoint(self._h, _ptr(xyz), _ptr(q), _ptr(gE), _ptr(grad_x),
+                                       _ptr(grad_q)), "se_adjoint")
 
     def status(self):
         st = ctypes.c_int()
