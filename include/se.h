@@ -179,6 +179,43 @@ int se_copy_grid(se_plan *plan, int which, void *dst);
  * (double). Not part of the k-space result; provided for completeness. */
 int se_self_energy(const se_plan *plan, const double *q_host, int64_t n, double *E_self);
 
+/* ---- Ensembles: many independent systems in one launch sequence ----
+ * S systems, system s with N[s] charges in its own box [0, L[s])^3 and grid
+ * M[s]^3 (2 <= P <= M[s] <= 128), common xi and support P (c = 0.95, Eq. 4.2
+ * per system), evaluated by the single-precision pipeline (exact fixed-point
+ * spreading; SE_FP32 semantics) with one kernel launch per stage for all
+ * systems, replayed as one CUDA graph.  Positions, charges, forces and
+ * potentials are the systems' arrays concatenated in order: xyz [sum N][3],
+ * q [sum N], F [sum N][3], phi [sum N] (float, DEVICE).  E: DEVICE array of S
+ * doubles (E^L of each system, 1/2 sum q phi).  Limits: S <= 1024,
+ * sum N < 2^31, at most 8192 spreading tiles per system. */
+typedef struct se_batch se_batch;
+int se_batch_create(se_batch **out, int S, const int64_t *N, const double *L, const int *M,
+                    double xi, int P);
+int se_batch_destroy(se_batch *batch);
+int se_batch_set_stream(se_batch *batch, void *stream);
+/* Multiply phi, E and F by kc (default 1). */
+int se_batch_set_prefactor(se_batch *batch, double kc);
+/* Edge of the spreading tiles in grid cells (2..32, default 8). */
+int se_batch_set_tile(se_batch *batch, int tile);
+/* enable = 0: launch every kernel directly instead of replaying a graph. */
+int se_batch_set_graph(se_batch *batch, int enable);
+/* One evaluation of every system (F, phi, E may each be NULL). */
+int se_batch_evaluate(se_batch *batch, const void *xyz, const void *q, void *F, void *phi,
+                      double *E);
+/* Grid energies of the last evaluation (DEVICE array of S doubles), equal to
+ * E to rounding. */
+int se_batch_grid_energy(se_batch *batch, double *E_grid);
+/* Worst input check over the systems of the last evaluation (SE_OK,
+ * SE_WARN_NONNEUTRAL or SE_ERR_NONFINITE); waits for the stream. */
+int se_batch_get_status(se_batch *batch, int *status);
+/* Autotuner: times `reps` evaluations with each tile edge in candidates[0..
+ * ncand) (CUDA events, after warm-up) and keeps the fastest; reports it in
+ * *best_tile and its time per evaluation in *best_ms. */
+int se_batch_autotune(se_batch *batch, const void *xyz, const void *q, void *F, void *phi,
+                      double *E, const int *candidates, int ncand, int reps, int *best_tile,
+                      float *best_ms);
+
 /* se_spread_noalloc -- the spreading step without any device allocation.
  * The paper has no counterpart: this exists for callers that cannot call
  * cudaMalloc (a program that reserves all device memory at start-up and

@@ -49,6 +49,17 @@ SIGNATURES = {
     "se_plan_set_timing": (_i, [_vp, _i]),
     "se_plan_get_timing": (_i, [_vp, _dp, _i, ctypes.POINTER(_i64), _i]),
     "se_spread_noalloc": (_i, [_vp, _vp, _i64, _d, _d, _i, _i, _vp, _vp]),
+    "se_batch_create": (_i, [ctypes.POINTER(_vp), _i, _vp, _vp, _vp, _d, _i]),
+    "se_batch_destroy": (_i, [_vp]),
+    "se_batch_set_stream": (_i, [_vp, _vp]),
+    "se_batch_set_prefactor": (_i, [_vp, _d]),
+    "se_batch_set_tile": (_i, [_vp, _i]),
+    "se_batch_set_graph": (_i, [_vp, _i]),
+    "se_batch_evaluate": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "se_batch_grid_energy": (_i, [_vp, _vp]),
+    "se_batch_get_status": (_i, [_vp, ctypes.POINTER(_i)]),
+    "se_batch_autotune": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i, _i, ctypes.POINTER(_i),
+                               ctypes.POINTER(ctypes.c_float)]),
     "se_strerror": (ctypes.c_char_p, [_i]),
     "se_version": (_i, []),
 }

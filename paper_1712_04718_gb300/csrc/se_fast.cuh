@@ -28,6 +28,25 @@ namespace se {
 
 constexpr int kFastKC = 8;        // spectrum columns per block in the y and x passes
 
+// cudaLaunchKernelEx with programmatic stream serialization (pdl = true): the
+// kernel may be scheduled while its predecessor drains and waits for that
+// predecessor's results in griddepcontrol.wait.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_ex(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+                      bool pdl, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? attr : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -250,27 +269,19 @@ __device__ __forceinline__ unsigned long long fx_join2(unsigned a0, unsigned a1)
     return ((unsigned long long)(long long)(int)a1 << 21) + (unsigned long long)a0;
 }
 
+// Spread of one tile (Eq. 3.5) into the fixed-point grid g64.  tile_start
+// holds the tile's particle range in `sorted`; fxs is the fixed-point scale.
+// Called by one whole block (uniformly: the early return is per block).
 template <int P>
-__global__ void __launch_bounds__(256)
-k_fspread(const f4* __restrict__ sorted, const int* __restrict__ tile_start,
-          int* __restrict__ tile_count, unsigned long long* __restrict__ g64,
-          const KParams<float> kp, const Acc* __restrict__ acc, int slab) {
+__device__ __forceinline__ void spread_tile(const f4* __restrict__ sorted,
+                                            const int* __restrict__ tile_start,
+                                            unsigned long long* __restrict__ g64,
+                                            const KParams<float>& kp, float fxs, int slab,
+                                            int tile, unsigned* hi, float* sE3) {
     constexpr int D = pick_d(P), G = P / D, GPW = 32 / G;
-    SE_STAMP(2, 0);
-    pdl_wait();
-    pdl_launch_next();
-    SE_STAMP(2, 1);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned* hi = reinterpret_cast<unsigned*>(smem_raw);
-    __shared__ float sE3[P];
-    // the counters are consumed: clear them for the next evaluation
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < kp.ntiles; k += gridDim.x * blockDim.x)
-        tile_count[k] = 0;
-    const int tile = blockIdx.x;
     const int pbeg = tile_start[tile], pend = tile_start[tile + 1];
     if (pbeg == pend) return;
     if (threadIdx.x < P) sE3[threadIdx.x] = kp.E3[threadIdx.x];
-    const float fxs = acc->fx_scale;
     const int nT = kp.nT, M = kp.M, TT = kp.tile;
     const int tz = tile % nT, ty = (tile / nT) % nT, tx = tile / (nT * nT);
     const int t0x = tx * TT, t0y = ty * TT, t0z = tz * TT;
@@ -361,6 +372,24 @@ k_fspread(const f4* __restrict__ sorted, const int* __restrict__ tile_start,
     }
 }
 
+template <int P>
+__global__ void __launch_bounds__(256)
+k_fspread(const f4* __restrict__ sorted, const int* __restrict__ tile_start,
+          int* __restrict__ tile_count, unsigned long long* __restrict__ g64,
+          const KParams<float> kp, const Acc* __restrict__ acc, int slab) {
+    SE_STAMP(2, 0);
+    pdl_wait();
+    pdl_launch_next();
+    SE_STAMP(2, 1);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ float sE3[P];
+    // the counters are consumed: clear them for the next evaluation
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < kp.ntiles; k += gridDim.x * blockDim.x)
+        tile_count[k] = 0;
+    spread_tile<P>(sorted, tile_start, g64, kp, acc->fx_scale, slab, blockIdx.x,
+                   reinterpret_cast<unsigned*>(smem_raw), sE3);
+}
+
 // ---------------------------------------------------------------------------
 // The 3-D transform in three kernels.  tw[r] = (cos, sin)(2 pi r / M); the
 // forward transform uses e^{-i}, the inverse e^{+i}; both unnormalised.
@@ -387,21 +416,16 @@ __host__ __device__ inline size_t slab_smem_bytes(int M) {
     return (size_t)M * sizeof(float2) + slab_a_bytes(M) + Mh * SP * sizeof(float2);
 }
 
-__global__ void __launch_bounds__(kSlabThreads)
-k_slab_fwd(const long long* __restrict__ g64, float2* __restrict__ C,
-           const float2* __restrict__ tw_g, int M, const Acc* __restrict__ acc) {
-    SE_STAMP(3, 0);
-    pdl_wait();
-    pdl_launch_next();
-    SE_STAMP(3, 1);
-    extern __shared__ __align__(16) unsigned char sm[];
+// Forward 2-D transform (z real-to-complex, then y) of x-slab x.
+__device__ __forceinline__ void slab_fwd_body(const long long* __restrict__ g64,
+                                              float2* __restrict__ C,
+                                              const float2* __restrict__ tw_g, int M, float inv,
+                                              int x, unsigned char* sm) {
     const int Mh = M / 2 + 1, SP = M + 1;
     float2* tw = reinterpret_cast<float2*>(sm);
     float* S = reinterpret_cast<float*>(sm + (size_t)M * sizeof(float2));
     float2* T = reinterpret_cast<float2*>(sm + (size_t)M * sizeof(float2) + slab_a_bytes(M));
-    const int x = blockIdx.x;
     load_twiddles(tw, tw_g, M);
-    const float inv = acc->fx_inv;
     const long long* src = g64 + (size_t)x * M * M;
     for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
         const int y = e / M, z = e - y * M;
@@ -421,21 +445,31 @@ k_slab_fwd(const long long* __restrict__ g64, float2* __restrict__ C,
     SE_STAMP(3, 4);
 }
 
-__global__ void __launch_bounds__(256)
-k_xpass(float2* __restrict__ C, const float2* __restrict__ tw_g, const float* __restrict__ green,
-        int M, float invM3, double* __restrict__ partials, unsigned* ticket, Acc* acc,
-        double e_scale, double* E_out) {
-    SE_STAMP(4, 0);
+#ifndef SE_BATCH_TU
+__global__ void __launch_bounds__(kSlabThreads)
+k_slab_fwd(const long long* __restrict__ g64, float2* __restrict__ C,
+           const float2* __restrict__ tw_g, int M, const Acc* __restrict__ acc) {
+    SE_STAMP(3, 0);
     pdl_wait();
     pdl_launch_next();
-    SE_STAMP(4, 1);
+    SE_STAMP(3, 1);
+    extern __shared__ __align__(16) unsigned char sm[];
+    slab_fwd_body(g64, C, tw_g, M, acc->fx_inv, blockIdx.x, sm);
+}
+#endif  // SE_BATCH_TU
+
+// x pass of work item `item` = (ky, kz chunk): forward DFT along x, scaling
+// by G/M^3 with the grid energy (returned, valid in thread 0), inverse DFT.
+__device__ __forceinline__ df2 xpass_body(float2* __restrict__ C, const float2* __restrict__ tw_g,
+                                          const float* __restrict__ green, int M, float invM3,
+                                          int item) {
     __shared__ float2 tw[kFastMaxM];
     __shared__ float2 s[kFastMaxM * kFastKC];
     __shared__ float2 s2[kFastMaxM * kFastKC];
     __shared__ df2 sbuf[32];
     const int Mh = M / 2 + 1;
     const int nch = (Mh + kFastKC - 1) / kFastKC;
-    const int y = blockIdx.x / nch, c0 = (blockIdx.x % nch) * kFastKC;
+    const int y = item / nch, c0 = (item % nch) * kFastKC;
     const int nc = min(kFastKC, Mh - c0);
     load_twiddles(tw, tw_g, M);
     for (int e = threadIdx.x; e < M * nc; e += blockDim.x) {
@@ -461,8 +495,21 @@ k_xpass(float2* __restrict__ C, const float2* __restrict__ tw_g, const float* __
     __syncthreads();
     dft_c2c<2, 2>(s2, kFastKC, 1, C + (size_t)y * Mh + c0, (size_t)M * Mh, 1, M, M, nc, tw, M, 1.0f);
     SE_STAMP(4, 4);
+    return block_sum_df(en, sbuf);
+}
+
+#ifndef SE_BATCH_TU
+__global__ void __launch_bounds__(256)
+k_xpass(float2* __restrict__ C, const float2* __restrict__ tw_g, const float* __restrict__ green,
+        int M, float invM3, double* __restrict__ partials, unsigned* ticket, Acc* acc,
+        double e_scale, double* E_out) {
+    SE_STAMP(4, 0);
+    pdl_wait();
+    pdl_launch_next();
+    SE_STAMP(4, 1);
+    __shared__ df2 sbuf[32];
+    const df2 tot = xpass_body(C, tw_g, green, M, invM3, blockIdx.x);
     float* pf = reinterpret_cast<float*>(partials);
-    const df2 tot = block_sum_df(en, sbuf);
     if (threadIdx.x == 0) {
         pf[2 * blockIdx.x] = tot.hi;
         pf[2 * blockIdx.x + 1] = tot.lo;
@@ -478,21 +525,17 @@ k_xpass(float2* __restrict__ C, const float2* __restrict__ tw_g, const float* __
         *ticket = 0u;
     }
 }
+#endif  // SE_BATCH_TU
 
-__global__ void __launch_bounds__(kSlabThreads)
-k_slab_inv(const float2* __restrict__ C, float* __restrict__ R, const float2* __restrict__ tw_g,
-           int M) {
-    SE_STAMP(5, 0);
-    pdl_wait();
-    pdl_launch_next();
-    SE_STAMP(5, 1);
-    extern __shared__ __align__(16) unsigned char sm[];
+// Inverse 2-D transform (y, then z complex-to-real) of x-slab x into R.
+__device__ __forceinline__ void slab_inv_body(const float2* __restrict__ C, float* __restrict__ R,
+                                              const float2* __restrict__ tw_g, int M, int x,
+                                              unsigned char* sm) {
     const int Mh = M / 2 + 1, SP = M + 1;
     float2* tw = reinterpret_cast<float2*>(sm);
     float* S = reinterpret_cast<float*>(sm + (size_t)M * sizeof(float2));
     float2* A = reinterpret_cast<float2*>(S);   // the slab, before S is needed
     float2* T = reinterpret_cast<float2*>(sm + (size_t)M * sizeof(float2) + slab_a_bytes(M));
-    const int x = blockIdx.x;
     load_twiddles(tw, tw_g, M);
     const float2* src = C + (size_t)x * M * Mh;
     for (int e = threadIdx.x; e < M * Mh; e += blockDim.x) A[e] = src[e];
@@ -522,10 +565,24 @@ k_slab_inv(const float2* __restrict__ C, float* __restrict__ R, const float2* __
     SE_STAMP(5, 4);
 }
 
+#ifndef SE_BATCH_TU
+__global__ void __launch_bounds__(kSlabThreads)
+k_slab_inv(const float2* __restrict__ C, float* __restrict__ R, const float2* __restrict__ tw_g,
+           int M) {
+    SE_STAMP(5, 0);
+    pdl_wait();
+    pdl_launch_next();
+    SE_STAMP(5, 1);
+    extern __shared__ __align__(16) unsigned char sm[];
+    slab_inv_body(C, R, tw_g, M, blockIdx.x, sm);
+}
+#endif  // SE_BATCH_TU
+
 }  // namespace se
 
 namespace se {
 
+#ifndef SE_BATCH_TU
 // fixed-point grid -> real grid (for inspection of the spread grid)
 __global__ void __launch_bounds__(256)
 k_fx_to_real(const long long* __restrict__ g64, float* __restrict__ dst, long long n,
@@ -540,5 +597,6 @@ k_fx_to_real(const long long* __restrict__ g64, float* __restrict__ dst, long lo
         dst[i] = fmaf(hi, 4294967296.0f, lo) * inv;
     }
 }
+#endif  // SE_BATCH_TU
 
 }  // namespace se

@@ -93,7 +93,7 @@ __device__ __forceinline__ void pdl_launch_next() { asm volatile("griddepcontrol
 // Optional phase tracing (build with -DSE_TRACE): thread 0 of each block
 // records %globaltimer at phase boundaries of the single-precision kernels
 // into se_trace_buf[kernel][block][phase]; compiled out otherwise.
-#ifdef SE_TRACE
+#if defined(SE_TRACE) && !defined(SE_BATCH_TU)
 constexpr int kTraceKernels = 8, kTraceBlocks = 2048, kTracePhases = 8;
 __device__ unsigned long long se_trace_buf[kTraceKernels][kTraceBlocks][kTracePhases];
 #define SE_STAMP(kid, ph)                                                                   \
@@ -560,12 +560,89 @@ k_scale(C* __restrict__ cgrid, const double* __restrict__ green, int M, double i
 // Results are scattered to the caller's order; the energy sum q phi is
 // reduced per block and finished by the last block.
 // ---------------------------------------------------------------------------
+// Potential and force sums of one particle on the grid (Eq. 3.9 and the
+// analytic force of Sec. 3.1), for this lane's z points: returns the partial
+// sums vphi, vfx, vfy, vfz (to be reduced over the particle's G lanes).
+template <typename T, int P>
+__device__ __forceinline__ void gather_particle(const v4_t<T>& v, const T* __restrict__ grid,
+                                                const KParams<T>& kp, const T* sE3, int k, T& vphi,
+                                                T& vfx, T& vfy, T& vfz) {
+    constexpr int D = pick_d(P), G = P / D;
+    const int M = kp.M;
+    T t;
+    const int cx = cell_of(v.x, kp.invh, M, &t);
+    const T ux = centre_offset(t, cx);
+    const int cy = cell_of(v.y, kp.invh, M, &t);
+    const T uy = centre_offset(t, cy);
+    const int cz = cell_of(v.z, kp.invh, M, &t);
+    const T uz = centre_offset(t, cz);
+    T gy[P], dgy[P];
+    int jy[P];
+    fgg<T, P>(uy, kp.beta, kp.E3, gy);
+    const int i0x = cx - P / 2 + 1, i0y = cy - P / 2 + 1;
+#pragma unroll
+    for (int b = 0; b < P; ++b) {
+        dgy[b] = (T(b) - T(0.5) * T(P - 1) - uy) * gy[b];
+        jy[b] = wrap_index(i0y + b, M);
+    }
+    T gz[D], dgz[D];
+    int jz[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const int c = k + j * G;
+        const T dz = T(c) - T(0.5) * T(P - 1) - uz;
+        gz[j] = expT(-kp.beta * dz * dz);
+        dgz[j] = dz * gz[j];
+        jz[j] = wrap_index(cz - P / 2 + 1 + c, M);
+    }
+    T acc0[D], accx[D], accy[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) acc0[j] = accx[j] = accy[j] = T(0);
+    const T Bx = expT(T(2) * kp.beta * ux);
+    T px = expT(-kp.beta * ux * (ux + T(P - 1)));
+    // small supports: the whole x loop unrolled, so that every load of
+    // the particle's P^3 grid values is in flight at once
+#pragma unroll(P <= 8 ? P : 1)
+    for (int a = 0; a < P; ++a) {
+        const T gxa = px * sE3[a];
+        const T dgxa = (T(a) - T(0.5) * T(P - 1) - ux) * gxa;
+        px *= Bx;
+        const int jx = wrap_index(i0x + a, M);
+        T tb0[D], tby[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) tb0[j] = tby[j] = T(0);
+#pragma unroll
+        for (int b = 0; b < P; ++b) {
+            const T* row = grid + ((size_t)jx * M + jy[b]) * M;
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                const T hv = __ldg(row + jz[j]);
+                tb0[j] += gy[b] * hv;
+                tby[j] += dgy[b] * hv;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            acc0[j] += gxa * tb0[j];
+            accx[j] += dgxa * tb0[j];
+            accy[j] += gxa * tby[j];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        vphi += gz[j] * acc0[j];
+        vfx += gz[j] * accx[j];
+        vfy += gz[j] * accy[j];
+        vfz += dgz[j] * acc0[j];
+    }
+}
+
 template <typename T, int P>
 __global__ void __launch_bounds__(256)
 k_gather(const v4_t<T>* __restrict__ sorted, const int* __restrict__ perm,
-         const T* __restrict__ grid, T* __restrict__ phi, T* __restrict__ F,
-         const KParams<T> kp, double* __restrict__ partials, unsigned* ticket, Acc* acc,
-         double e_scale, double* E_out, const double* __restrict__ adj) {
+ const T* __restrict__ grid, T* __restrict__ phi, T* __restrict__ F,
+ const KParams<T> kp, double* __restrict__ partials, unsigned* ticket, Acc* acc,
+ double e_scale, double* E_out, const double* __restrict__ adj) {
     constexpr int D = pick_d(P), G = P / D, GPW = 32 / G;
     constexpr bool kSingle = sizeof(T) == sizeof(float);
     SE_STAMP(6, 0);
@@ -587,142 +664,77 @@ k_gather(const v4_t<T>* __restrict__ sorted, const int* __restrict__ perm,
     double e_loc = 0.0;
     df2 e_df = df_from(0.0f);
     for (int pb = blockIdx.x * gpb + warp * GPW; pb < kp.N; pb += gridDim.x * gpb) {
-        const int p = pb + gi;
-        const bool valid = (gi < GPW) && (p < kp.N);
-        T vphi = T(0), vfx = T(0), vfy = T(0), vfz = T(0), qq = T(0);
-        if (valid) {
-            const v4_t<T> v = sorted[p];
-            qq = v.w;
-            T t;
-            const int cx = cell_of(v.x, kp.invh, M, &t);
-            const T ux = centre_offset(t, cx);
-            const int cy = cell_of(v.y, kp.invh, M, &t);
-            const T uy = centre_offset(t, cy);
-            const int cz = cell_of(v.z, kp.invh, M, &t);
-            const T uz = centre_offset(t, cz);
-            T gy[P], dgy[P];
-            int jy[P];
-            fgg<T, P>(uy, kp.beta, kp.E3, gy);
-            const int i0x = cx - P / 2 + 1, i0y = cy - P / 2 + 1;
+const int p = pb + gi;
+const bool valid = (gi < GPW) && (p < kp.N);
+T vphi = T(0), vfx = T(0), vfy = T(0), vfz = T(0), qq = T(0);
+if (valid) {
+    const v4_t<T> v = sorted[p];
+    qq = v.w;
+    gather_particle<T, P>(v, grid, kp, sE3, k, vphi, vfx, vfy, vfz);
+}
+SE_STAMP(6, 2);
+// reduce over the G lanes of each particle (lane 0 of the group ends with the sum)
 #pragma unroll
-            for (int b = 0; b < P; ++b) {
-                dgy[b] = (T(b) - T(0.5) * T(P - 1) - uy) * gy[b];
-                jy[b] = wrap_index(i0y + b, M);
-            }
-            T gz[D], dgz[D];
-            int jz[D];
-#pragma unroll
-            for (int j = 0; j < D; ++j) {
-                const int c = k + j * G;
-                const T dz = T(c) - T(0.5) * T(P - 1) - uz;
-                gz[j] = expT(-kp.beta * dz * dz);
-                dgz[j] = dz * gz[j];
-                jz[j] = wrap_index(cz - P / 2 + 1 + c, M);
-            }
-            T acc0[D], accx[D], accy[D];
-#pragma unroll
-            for (int j = 0; j < D; ++j) acc0[j] = accx[j] = accy[j] = T(0);
-            const T Bx = expT(T(2) * kp.beta * ux);
-            T px = expT(-kp.beta * ux * (ux + T(P - 1)));
-            // small supports: the whole x loop unrolled, so that every load of
-            // the particle's P^3 grid values is in flight at once
-#pragma unroll(P <= 8 ? P : 1)
-            for (int a = 0; a < P; ++a) {
-                const T gxa = px * sE3[a];
-                const T dgxa = (T(a) - T(0.5) * T(P - 1) - ux) * gxa;
-                px *= Bx;
-                const int jx = wrap_index(i0x + a, M);
-                T tb0[D], tby[D];
-#pragma unroll
-                for (int j = 0; j < D; ++j) tb0[j] = tby[j] = T(0);
-#pragma unroll
-                for (int b = 0; b < P; ++b) {
-                    const T* row = grid + ((size_t)jx * M + jy[b]) * M;
-#pragma unroll
-                    for (int j = 0; j < D; ++j) {
-                        const T hv = __ldg(row + jz[j]);
-                        tb0[j] += gy[b] * hv;
-                        tby[j] += dgy[b] * hv;
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < D; ++j) {
-                    acc0[j] += gxa * tb0[j];
-                    accx[j] += dgxa * tb0[j];
-                    accy[j] += gxa * tby[j];
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < D; ++j) {
-                vphi += gz[j] * acc0[j];
-                vfx += gz[j] * accx[j];
-                vfy += gz[j] * accy[j];
-                vfz += dgz[j] * acc0[j];
-            }
-        }
-        SE_STAMP(6, 2);
-        // reduce over the G lanes of each particle (lane 0 of the group ends with the sum)
-#pragma unroll
-        for (int o = 1; o < G; o <<= 1) {
-            const T a0 = __shfl_down_sync(0xffffffffu, vphi, o);
-            const T a1 = __shfl_down_sync(0xffffffffu, vfx, o);
-            const T a2 = __shfl_down_sync(0xffffffffu, vfy, o);
-            const T a3 = __shfl_down_sync(0xffffffffu, vfz, o);
-            if (k + o < G) {
-                vphi += a0;
-                vfx += a1;
-                vfy += a2;
-                vfz += a3;
-            }
-        }
-        if (valid && k == 0) {
-            const T ph = vphi * kp.phi_scale;
-            const T fs = qq * kp.F_scale;
-            const int orig = perm[p];
-            if (phi) phi[orig] = ph * phi_mul;
-            if (F) {
-                const T fm = fs * F_mul;
-                F[3 * orig] = fm * vfx;
-                F[3 * orig + 1] = fm * vfy;
-                F[3 * orig + 2] = fm * vfz;
-            }
-            if (kSingle)
-                e_df = df_add(e_df, df_from((float)(qq * ph)));
-            else
-                e_loc += (double)qq * (double)ph;
-        }
+for (int o = 1; o < G; o <<= 1) {
+    const T a0 = __shfl_down_sync(0xffffffffu, vphi, o);
+    const T a1 = __shfl_down_sync(0xffffffffu, vfx, o);
+    const T a2 = __shfl_down_sync(0xffffffffu, vfy, o);
+    const T a3 = __shfl_down_sync(0xffffffffu, vfz, o);
+    if (k + o < G) {
+        vphi += a0;
+        vfx += a1;
+        vfy += a2;
+        vfz += a3;
+    }
+}
+if (valid && k == 0) {
+    const T ph = vphi * kp.phi_scale;
+    const T fs = qq * kp.F_scale;
+    const int orig = perm[p];
+    if (phi) phi[orig] = ph * phi_mul;
+    if (F) {
+        const T fm = fs * F_mul;
+        F[3 * orig] = fm * vfx;
+        F[3 * orig + 1] = fm * vfy;
+        F[3 * orig + 2] = fm * vfz;
+    }
+    if (kSingle)
+        e_df = df_add(e_df, df_from((float)(qq * ph)));
+    else
+        e_loc += (double)qq * (double)ph;
+}
     }
     SE_STAMP(6, 3);
     if (kSingle) {
-        // double-float partials: (hi, lo) floats per block
-        float* pf = reinterpret_cast<float*>(partials);
-        const df2 r = block_sum_df(e_df, sbuf_df);
-        SE_STAMP(6, 4);
-        if (threadIdx.x == 0) {
-            pf[2 * blockIdx.x] = r.hi;
-            pf[2 * blockIdx.x + 1] = r.lo;
-        }
-        const bool lastb = last_block(ticket);
-        SE_STAMP(6, 5);
-        if (!lastb) return;
-        const df2 t = sum_partials_df(pf, gridDim.x, 1, 0, sbuf_df);
-        SE_STAMP(6, 6);
-        if (threadIdx.x == 0) {
-            const double s = df_to_double(t);
-            acc->e_gather = s;
-            if (E_out) *E_out = e_scale * s;
-            *ticket = 0u;
-        }
-        return;
+// double-float partials: (hi, lo) floats per block
+float* pf = reinterpret_cast<float*>(partials);
+const df2 r = block_sum_df(e_df, sbuf_df);
+SE_STAMP(6, 4);
+if (threadIdx.x == 0) {
+    pf[2 * blockIdx.x] = r.hi;
+    pf[2 * blockIdx.x + 1] = r.lo;
+}
+const bool lastb = last_block(ticket);
+SE_STAMP(6, 5);
+if (!lastb) return;
+const df2 t = sum_partials_df(pf, gridDim.x, 1, 0, sbuf_df);
+SE_STAMP(6, 6);
+if (threadIdx.x == 0) {
+    const double s = df_to_double(t);
+    acc->e_gather = s;
+    if (E_out) *E_out = e_scale * s;
+    *ticket = 0u;
+}
+return;
     }
     double r = block_sum(e_loc, sbuf);
     if (threadIdx.x == 0) partials[blockIdx.x] = r;
     if (!last_block(ticket)) return;
     const double s = sum_partials(partials, gridDim.x, 1, 0, sbuf);
     if (threadIdx.x == 0) {
-        acc->e_gather = s;
-        if (E_out) *E_out = e_scale * s;
-        *ticket = 0u;
+acc->e_gather = s;
+if (E_out) *E_out = e_scale * s;
+*ticket = 0u;
     }
 }
 

@@ -236,3 +236,87 @@ def se_energy_force_host(plan, xyz, q):
 
 def se_plan_destroy(plan):
     plan.close()
+
+
+class Batch:
+    """S independent systems evaluated together (se_batch_*): Ns, Ls, Ms per
+    system, common xi and P; float32 arrays concatenated over the systems."""
+
+    def __init__(self, Ns, Ls, Ms, xi, P, tile=None, prefactor=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libse needs a CUDA device; none is available")
+        self._lib = nat.load()
+        self.S = len(Ns)
+        self.Ns = np.asarray(Ns, dtype=np.int64)
+        self.Ls = np.asarray(Ls, dtype=np.float64)
+        self.Ms = np.asarray(Ms, dtype=np.int32)
+        self.xi, self.P = float(xi), int(P)
+        self.offsets = np.concatenate([[0], np.cumsum(self.Ns)])
+        self.Ntot = int(self.offsets[-1])
+        self._h = ctypes.c_void_p()
+        nat.check(self._lib.se_batch_create(
+            ctypes.byref(self._h), self.S, self.Ns.ctypes.data_as(ctypes.c_void_p),
+            self.Ls.ctypes.data_as(ctypes.c_void_p), self.Ms.ctypes.data_as(ctypes.c_void_p),
+            self.xi, self.P), "se_batch_create")
+        if tile:
+            nat.check(self._lib.se_batch_set_tile(self._h, int(tile)), "se_batch_set_tile")
+        if prefactor is not None:
+            nat.check(self._lib.se_batch_set_prefactor(self._h, float(prefactor)),
+                      "se_batch_set_prefactor")
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.se_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self):
+        s = torch.cuda.current_stream().cuda_stream
+        nat.check(self._lib.se_batch_set_stream(self._h, ctypes.c_void_p(s)), "se_batch_set_stream")
+
+    def set_graph(self, enable=True):
+        nat.check(self._lib.se_batch_set_graph(self._h, int(bool(enable))), "se_batch_set_graph")
+
+    def evaluate(self, xyz, q, F=None, phi=None, E=None):
+        """Returns (E [S] float64, F [Ntot,3], phi [Ntot]) CUDA tensors."""
+        if F is None:
+            F = torch.empty((self.Ntot, 3), dtype=torch.float32, device=xyz.device)
+        if phi is None:
+            phi = torch.empty((self.Ntot,), dtype=torch.float32, device=xyz.device)
+        if E is None:
+            E = torch.empty((self.S,), dtype=torch.float64, device=xyz.device)
+        self._stream()
+        nat.check(self._lib.se_batch_evaluate(self._h, _ptr(xyz), _ptr(q), _ptr(F), _ptr(phi),
+                                              _ptr(E)), "se_batch_evaluate")
+        return E, F, phi
+
+    def grid_energy(self):
+        Eg = torch.empty((self.S,), dtype=torch.float64, device="cuda")
+        self._stream()
+        nat.check(self._lib.se_batch_grid_energy(self._h, _ptr(Eg)), "se_batch_grid_energy")
+        return Eg
+
+    def status(self):
+        st = ctypes.c_int()
+        nat.check(self._lib.se_batch_get_status(self._h, ctypes.byref(st)), "se_batch_get_status")
+        return st.value
+
+    def autotune(self, xyz, q, candidates=(4, 6, 8, 10), reps=10):
+        """Time each tile edge and keep the fastest; returns (tile, ms per evaluation)."""
+        c = np.asarray(candidates, dtype=np.int32)
+        F = torch.empty((self.Ntot, 3), dtype=torch.float32, device=xyz.device)
+        phi = torch.empty((self.Ntot,), dtype=torch.float32, device=xyz.device)
+        E = torch.empty((self.S,), dtype=torch.float64, device=xyz.device)
+        best = ctypes.c_int()
+        ms = ctypes.c_float()
+        self._stream()
+        nat.check(self._lib.se_batch_autotune(self._h, _ptr(xyz), _ptr(q), _ptr(F), _ptr(phi),
+                                              _ptr(E), c.ctypes.data_as(ctypes.c_void_p), len(c),
+                                              int(reps), ctypes.byref(best), ctypes.byref(ms)),
+                  "se_batch_autotune")
+        return best.value, ms.value
