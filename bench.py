@@ -49,6 +49,10 @@ def parse_args():
                     help="bounded CPU work of the cpu_baseline leg")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip accuracy, e2e, at-target and cpu_baseline legs")
+    ap.add_argument("--tile", type=int, default=0,
+                    help="spreading tile edge (0 = autotune, JSON-cached)")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="spread variant (-1 = autotune with the tile; 3 sorted, 4 unsorted)")
     return ap.parse_args()
 
 
@@ -114,22 +118,32 @@ def workload(name):
     return x, q, w, prec
 
 
-def stage_work(w, prec, N):
+def stage_work(w, prec, N, fast):
     """Algorithmic work of each own kernel per launch: (kind, amount).
     spread: N P^3 weights, each a multiply and an add (2 flops);
     gather: N P^3 grid values, each two FMAs (4 flops);
-    scale: complex grid read+write and the FP64 G table (bytes);
-    bin/scatter: particle bytes moved."""
+    single-precision pipeline (fast): the slab kernels do the z and y direct
+    DFTs (M^3 (M/2+1) complex multiply-adds each: 8 flops complex, 4 for the
+    real-to-complex / complex-to-real one), the x pass two complex ones;
+    cuFFT pipeline: scale reads and writes the half spectrum and the G table
+    (bytes); bin/scatter: particle bytes."""
     P, M = w["P"], w["M"]
+    Mh = M // 2 + 1
     ts = 8 if prec == "fp64" else 4
-    nc = M * M * (M // 2 + 1)
-    return {
+    nc = M * M * Mh
+    work = {
         "spread": ("flop", 2.0 * N * P ** 3),
         "gather": ("flop", 4.0 * N * P ** 3),
-        "scale": ("byte", nc * (4 * ts + 8) + M ** 3 * ts),
         "bin": ("byte", N * (4 * ts + 8)),
         "scatter": ("byte", N * (4 * ts + 4 * ts + 8 + 4)),
     }
+    if fast:
+        work["fft_fwd"] = ("flop", 12.0 * M ** 3 * Mh)
+        work["scale"] = ("flop", 16.0 * M ** 3 * Mh)
+        work["fft_inv"] = ("flop", 12.0 * M ** 3 * Mh)
+    else:
+        work["scale"] = ("byte", nc * (4 * ts + 8) + M ** 3 * ts)
+    return work
 
 
 def run_ours(args):
@@ -148,12 +162,21 @@ def run_ours(args):
         torch.distributed.barrier()
     from paper_1712_04718_gb300 import se
 
+    if args.workload.startswith("ensemble"):
+        return run_ensemble(args, torch, se, ws, rank)
     x, q, w, prec = workload(args.workload)
     N = len(q)
     plan = se.Plan(N, w["L"], w["xi"], w["M"], w["P"], precision=prec)
     dt = plan.dtype
     xd = torch.tensor(x, dtype=dt, device="cuda")
     qd = torch.tensor(q, dtype=dt, device="cuda")
+    if args.tile or args.variant >= 0:
+        plan.set_tuning(max(0, args.variant), args.tile)
+    elif prec != "fp64":
+        from paper_1712_04718_gb300 import tuning
+        tuning.tune_plan(plan, xd, qd)
+    variant = plan.params()["spread_variant"]
+    tile = plan.params()["tile"]
     F = torch.empty((N, 3), dtype=dt, device="cuda")
     phi = torch.empty((N,), dtype=dt, device="cuda")
     Ed = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -211,9 +234,12 @@ def run_ours(args):
     value = ws * K / (total_ms / 1e3)
 
     # roofline of the dominant own kernel (average launch duration from events)
-    work = stage_work(w, prec, N)
+    fast = variant in (3, 4)
+    work = stage_work(w, prec, N, fast)
     per_launch_ms = {k: v / max(1, nstage) for k, v in stages.items()}
     own = ["bin", "scatter", "spread", "scale", "gather"]
+    if fast:
+        own += ["fft_fwd", "fft_inv"]   # the transforms are own kernels there
     dom = max(own, key=lambda k: per_launch_ms[k])
     kind, amount = work[dom]
     secs = per_launch_ms[dom] / 1e3
@@ -243,25 +269,136 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": args.workload, "N": N, "L": w["L"], "xi": w["xi"], "M": w["M"],
                    "P": w["P"], "precision": w["prec"], "parallelism": "replicas" if ws > 1 else "single",
-                   "l2": "flushed between steps (256 MiB write, untimed)"},
+                   "spread_variant": variant,
+                   "spread_tile": tile if variant != 4 else None,
+                   "pipeline": {3: "single-precision, no cuFFT, sorted spread",
+                                4: "single-precision, no cuFFT, unsorted spread"}.get(variant, "cuFFT"),
+                   "l2": "flushed between steps (256 MiB write + 256 MiB read, untimed)"},
         "stages_us_per_eval": {k: v / max(1, nstage) * 1e3 for k, v in stages.items()},
         "stages_note": "per-stage CUDA events, direct launches, %d evaluations (the headline "
                        "replays one CUDA graph per evaluation)" % nstage,
         "fft_us_per_eval": (stages["fft_fwd"] + stages["fft_inv"]) / max(1, nstage) * 1e3,
         "roofline": roof,
-        "gpu_launches": 5 * K,
-        "gpu_launches_note": "own kernels (bin, scatter, spread, scale, gather) per step; cuFFT kernels not counted",
+        "gpu_launches": {3: 7, 4: 5}.get(variant, 5) * K,
+        "gpu_launches_note": {
+            3: "own kernels per step: bin, scatter, spread, slab_fwd, xpass, slab_inv, gather",
+            4: "own kernels per step: spread (unsorted), slab_fwd, xpass, slab_inv, gather"}.get(
+                variant, "own kernels per step: bin, scatter, spread, scale, gather (+ cuFFT)"),
         "clocks": clk,
     }
 
     if rank == 0 and not args.no_extras:
         out["accuracy"] = accuracy(se, torch, x, q, w, prec, F)
-        out["e2e"] = e2e(se, torch, x, q, w, prec, max(20, min(K, 500)))
+        out["e2e"] = e2e(se, torch, x, q, w, prec, max(20, min(K, 500)), (variant, tile))
         if args.workload == DEFAULT_WORKLOAD:
             out["at_target"] = at_target(se, torch, x, q, w, prec, K, flush)
         out["no_graph"] = no_graph(se, torch, plan, xd, qd, F, phi, Ed, flush, min(K, 1000))
         out["cpu_baseline"] = cpu_baseline(x, q, w, args.cpu_seconds)
     plan.close()
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def run_ensemble(args, torch, se, ws, rank):
+    """The batched ensemble: every rank evaluates its share of the systems
+    (round robin) through one se_batch; value = evaluations of the whole
+    ensemble per second of the slowest rank (strong scaling: the ensemble is
+    fixed)."""
+    from paper_1712_04718_gb300 import systems, tuning
+    w = systems.WORKLOADS[args.workload]
+    ens = systems.ensemble(S=w["S"], spacing=w["spacing"])
+    mine = ens[rank::ws]
+    Ns = [len(d["q"]) for d in mine]
+    b = se.Batch(Ns, [d["L"] for d in mine], [d["M"] for d in mine], w["xi"], w["P"])
+    xd = torch.tensor(np.concatenate([d["x"] for d in mine]), device="cuda")
+    qd = torch.tensor(np.concatenate([d["q"] for d in mine]), device="cuda")
+    tile, _, _ = tuning.tune_batch(b, xd, qd)
+    Ntot = int(sum(Ns))
+    F = torch.empty((Ntot, 3), dtype=torch.float32, device="cuda")
+    phi = torch.empty((Ntot,), dtype=torch.float32, device="cuda")
+    E = torch.empty((len(mine),), dtype=torch.float64, device="cuda")
+    flush_w = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    flush_r = torch.ones(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    flush_out = torch.empty((), dtype=torch.float32, device="cuda")
+
+    def flush():
+        flush_w.zero_()
+        torch.sum(flush_r, dim=0, out=flush_out)
+
+    for _ in range(max(3, args.warmup)):
+        flush()
+        b.evaluate(xd, qd, F, phi, E)
+    torch.cuda.synchronize()
+    K = args.steps
+    st = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    en = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for i in range(K):
+        flush()
+        st[i].record()
+        b.evaluate(xd, qd, F, phi, E)
+        en[i].record()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    total_ms = sum(a.elapsed_time(c) for a, c in zip(st, en))
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = t.item()
+    ms_step = total_ms / K
+    Nall = sum(len(d["q"]) for d in ens)
+    out = {
+        "metric": METRIC, "value": K / (total_ms / 1e3), "unit": "ensemble evals/s",
+        "n_gpus": ws, "steps": K, "warmup": args.warmup, "ms_per_step": ms_step,
+        "ns_per_atom": ms_step * 1e6 / Nall, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "systems": len(ens), "atoms": Nall,
+                   "M_range": [min(d["M"] for d in ens), max(d["M"] for d in ens)],
+                   "P": w["P"], "xi": w["xi"], "parallelism": "systems sharded over ranks",
+                   "spread_tile": tile, "l2": "flushed between steps (untimed)"},
+        "gpu_launches": 8 * K, "clocks": clk,
+    }
+    if rank == 0 and not args.no_extras:
+        errs = []
+        off = np.concatenate([[0], np.cumsum(Ns)])
+        for s in range(0, len(mine), max(1, len(mine) // 4)):
+            d = mine[s]
+            _, Fref, _ = reference_forces(se, torch, d["x"], d["q"], dict(L=d["L"], xi=w["xi"]))
+            errs.append(rel_rms(F[off[s]:off[s + 1]].double().cpu().numpy(), Fref))
+        out["accuracy"] = {"rel_rms_force_err_max_sampled": max(errs),
+                           "target": w["target_rel_force_err"],
+                           "target_met": max(errs) <= w["target_rel_force_err"],
+                           "systems_sampled": len(errs)}
+        hx = torch.empty_like(xd, device="cpu").pin_memory()
+        hq = torch.empty_like(qd, device="cpu").pin_memory()
+        hF = torch.empty_like(F, device="cpu").pin_memory()
+        hE = torch.empty_like(E, device="cpu").pin_memory()
+        hx.copy_(xd)
+        hq.copy_(qd)
+        k2 = max(10, min(K, 200))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            xd.copy_(hx, non_blocking=True)
+            qd.copy_(hq, non_blocking=True)
+            b.evaluate(xd, qd, F, phi, E)
+            hF.copy_(F, non_blocking=True)
+            hE.copy_(E, non_blocking=True)
+            torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        out["e2e"] = {"value": k2 / (t1 - t0), "unit": "ensemble evals/s", "steps": k2,
+                      "h2d_bytes_per_step": hx.numel() * 4 + hq.numel() * 4,
+                      "d2h_bytes_per_step": hF.numel() * 4 + hE.numel() * 8}
+    b.close()
     if ws > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
@@ -300,6 +437,9 @@ def at_target(se, torch, x, q, w, prec, K, flush):
         dt = plan.dtype
         xd = torch.tensor(x, dtype=dt, device="cuda")
         qd = torch.tensor(q, dtype=dt, device="cuda")
+        if prec != "fp64":
+            from paper_1712_04718_gb300 import tuning
+            tuning.tune_plan(plan, xd, qd)
         F = torch.empty((N, 3), dtype=dt, device="cuda")
         phi = torch.empty((N,), dtype=dt, device="cuda")
         for _ in range(10):
@@ -319,8 +459,10 @@ def at_target(se, torch, x, q, w, prec, K, flush):
             en[i].record()
         torch.cuda.synchronize()
         ms = sum(a.elapsed_time(b) for a, b in zip(st, en)) / k
+        variant = plan.params()["spread_variant"]
         plan.close()
-        return {"P": P, "value": 1e3 / ms, "unit": "evals/s", "ms_per_step": ms,
+        return {"P": P, "spread_variant": variant,
+                "value": 1e3 / ms, "unit": "evals/s", "ms_per_step": ms,
                 "ns_per_atom": ms * 1e6 / N, "rel_rms_force_err": err, "steps": k}
     return None
 
@@ -343,11 +485,13 @@ def no_graph(se, torch, plan, xd, qd, F, phi, Ed, flush, K):
     return {"value": 1e3 / ms, "unit": "evals/s", "ms_per_step": ms, "steps": K}
 
 
-def e2e(se, torch, x, q, w, prec, K):
+def e2e(se, torch, x, q, w, prec, K, cfg):
     """Host buffers through se_energy_force_host: H2D of xyz and q, the
     evaluation, D2H of F, phi and E, every step."""
     N = len(q)
     plan = se.Plan(N, w["L"], w["xi"], w["M"], w["P"], precision=prec)
+    if prec != "fp64":
+        plan.set_tuning(*cfg)
     dt = plan.dtype
     hx = torch.tensor(x, dtype=dt).pin_memory()
     hq = torch.tensor(q, dtype=dt).pin_memory()

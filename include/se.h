@@ -97,12 +97,15 @@ int se_plan_set_stream(se_plan *plan, void *stream);
  * 3 = the single-precision pipeline without cuFFT (SE_FP32 or SE_FP32_PLAIN,
  * M <= 128; the default there): exact 64-bit fixed-point spreading, line DFTs
  * with the scaling fused into the x pass, kernels chained by programmatic
- * dependent launch.  tile = edge of a spreading tile in grid cells
- * (0 = automatic, else 2..32).  For benchmarking and tests. */
+ * dependent launch; 4 = the same pipeline with the particles left unsorted:
+ * one kernel adds every weight into a float grid with global reductions
+ * (the last bits of the grid then depend on the order of the additions).
+ * tile = edge of a spreading tile in grid cells (0 = automatic, else
+ * 2..32).  For benchmarking and tests. */
 int se_plan_set_tuning(se_plan *plan, int spread_variant, int tile);
 
 /* Derived parameters: out[0..9] = h, w, eta, alpha, c_g, m, tile edge,
- * spread variant in use (1 or 2), precision, prefactor.
+ * spread variant in use (1 to 4), precision, prefactor.
  * c_g = (2 xi^2 / (pi eta))^{3/2} is the Gaussian's normalisation (Eq. 3.5). */
 int se_plan_get_params(const se_plan *plan, double *out);
 
@@ -172,7 +175,9 @@ int se_energy_force_host(se_plan *plan, const void *xyz, const void *q,
 
 /* Copy one of the plan's grids into dst (device, M^3 values of the plan's
  * type, z fastest): which = 0 spread grid H (after se_spread), 1 scaled and
- * back-transformed grid Ht (after se_scale).  For tests and inspection. */
+ * back-transformed grid Ht (after se_scale).  With spread variant 4 the
+ * spread grid is cleared by se_scale: which = 0 after se_scale returns
+ * SE_ERR_ARG.  For tests and inspection. */
 int se_copy_grid(se_plan *plan, int which, void *dst);
 
 /* Self-energy term of Eq. 1.6, -kc xi / sqrt(pi) sum q^2, from HOST charges

@@ -167,8 +167,10 @@ k_bspread(const f4* __restrict__ sorted, const int* __restrict__ tile_start,
     __shared__ float sE3[P];
     const int s = tile_sys[blockIdx.x];
     const SysParams& sp = sys[s];
-    spread_tile<P>(sorted, tile_start + sp.t0, g64 + sp.g0, sp.kp, bacc[s].fx_scale, slab,
-                   blockIdx.x - sp.t0, reinterpret_cast<unsigned*>(smem_raw), sE3);
+    const int tile = blockIdx.x - sp.t0;
+    const int pb = tile_start[sp.t0 + tile];
+    spread_tile<P>(sorted + pb, tile_start[sp.t0 + tile + 1] - pb, g64 + sp.g0, sp.kp,
+                   bacc[s].fx_scale, slab, tile, reinterpret_cast<unsigned*>(smem_raw), sE3);
 }
 
 __global__ void __launch_bounds__(kSlabThreads)
@@ -234,8 +236,9 @@ k_bgather(const f4* __restrict__ sorted, const int* __restrict__ perm, const flo
             s = system_of(p0s, S, p);
             const f4 v = sorted[p];
             qq = v.w;
-            gather_particle<float, P>(v, R + sys[s].g0, sys[s].kp, sys[s].kp.E3, k, vphi, vfx,
-                                      vfy, vfz);
+            GatherPrep<float, P> g;
+            gather_prep<float, P>(v, sys[s].kp, k, g);
+            gather_accum<float, P>(g, R + sys[s].g0, sys[s].kp, sys[s].kp.E3, vphi, vfx, vfy, vfz);
         }
 #pragma unroll
         for (int o = 1; o < G; o <<= 1) {

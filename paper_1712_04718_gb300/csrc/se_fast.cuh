@@ -1,15 +1,14 @@
 // se_fast.cuh -- the single-precision SE pipeline for grids up to 128^3:
-// nine short kernels chained by programmatic dependent launch, no cuFFT.
+// six short kernels chained by programmatic dependent launch, no cuFFT.
 //
-//   k_fbin      tile of each particle, slot in its tile, q sums; clears the
-//               fixed-point spread grid
-//   k_fscatter  every block scans the tile counts; particles in tile order;
-//               block 0 publishes the tile offsets, the input checks and the
-//               fixed-point scale
+//   k_fbin      tile of each particle and a slot in the tile's bucket (a
+//               fixed-capacity list; full buckets spill to an overflow list),
+//               q sums and max |q|; clears the fixed-point spread grid
 //   k_fspread   Eq. 3.5, one CTA per tile, exact 64-bit fixed-point sums in
 //               shared memory (two native 32-bit atomics per weight), flushed
 //               with global 64-bit integer reductions: the grid is the same
-//               for any order of the additions
+//               for any order of the additions; a few more CTAs add the
+//               overflow list with global 64-bit atomics
 //   k_slab_fwd  per x-slab: forward DFT along z (real to complex; the
 //               fixed-point grid is converted to float here), then along y
 //   k_xpass     forward DFT along x, scaling by G(k)/M^3 (Eq. 3.6) with the
@@ -17,16 +16,23 @@
 //   k_slab_inv  per x-slab: inverse DFT along y, then along z (complex to real)
 //   (k_gather from se_kernels.cuh reads the real grid)
 //
+// Unsorted variant: k_fdirect replaces k_fbin and k_fspread by
+// one kernel that adds every weight straight into a float grid with global
+// reductions; k_slab_fwd_f reads that grid and clears it for the next call.
+//
 // The 1-D transforms are direct DFTs (M <= 128) written as small complex
 // matrix products with register tiles (se_dft.cuh); twiddles e^{-2 pi i r/M}
 // from a table in shared memory.
 #pragma once
+#include <type_traits>
+
 #include "se_dft.cuh"
 #include "se_kernels.cuh"
 
 namespace se {
 
 constexpr int kFastKC = 8;        // spectrum columns per block in the y and x passes
+constexpr int kLoadBatch = 8;     // global loads per thread issued together in the transforms
 
 // cudaLaunchKernelEx with programmatic stream serialization (pdl = true): the
 // kernel may be scheduled while its predecessor drains and waits for that
@@ -48,10 +54,16 @@ cudaError_t launch_ex(void (*kern)(KArgs...), int grid, int block, size_t smem, 
 }
 
 // ---------------------------------------------------------------------------
+// Tile buckets: particle slot s of tile t lives at bucket[t * cap + s].  The
+// bin kernel takes a slot with an atomic on the tile's count and writes the
+// particle there directly (no scan, no second pass); slots past cap go to an
+// overflow list that the spread kernel adds with global fixed-point atomics
+// (exact integers, so the grid does not depend on which path a particle took).
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_fbin(const T* __restrict__ xyz, const T* __restrict__ q, const KParams<T> kp,
-       int* __restrict__ tile_count, int* __restrict__ slot, int* __restrict__ tile_of,
+       int* __restrict__ tile_count, v4_t<T>* __restrict__ bucket, int cap,
+       int* __restrict__ over_idx, int* __restrict__ n_over, v4_t<T>* __restrict__ wrapped,
        double* __restrict__ partials, long long* __restrict__ g64) {
     SE_STAMP(0, 0);
     pdl_wait();
@@ -69,15 +81,26 @@ k_fbin(const T* __restrict__ xyz, const T* __restrict__ q, const KParams<T> kp,
     float qmax = 0.0f;
     int bad = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kp.N; i += gridDim.x * blockDim.x) {
-        T x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2], qq = q[i];
+        const T x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2], qq = q[i];
         if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(qq))) bad += 1;
+        v4_t<T> v;
+        v.x = wrap_coord(x, kp.L, kp.invL);
+        v.y = wrap_coord(y, kp.L, kp.invL);
+        v.z = wrap_coord(z, kp.L, kp.invL);
+        v.w = qq;
         T t;
-        int cx = cell_of(wrap_coord(x, kp.L, kp.invL), kp.invh, kp.M, &t);
-        int cy = cell_of(wrap_coord(y, kp.L, kp.invL), kp.invh, kp.M, &t);
-        int cz = cell_of(wrap_coord(z, kp.L, kp.invL), kp.invh, kp.M, &t);
-        int tile = ((cx / kp.tile) * kp.nT + cy / kp.tile) * kp.nT + cz / kp.tile;
-        slot[i] = atomicAdd(tile_count + tile, 1);
-        tile_of[i] = tile;
+        const int cx = cell_of(v.x, kp.invh, kp.M, &t);
+        const int cy = cell_of(v.y, kp.invh, kp.M, &t);
+        const int cz = cell_of(v.z, kp.invh, kp.M, &t);
+        const int tile = ((cx / kp.tile) * kp.nT + cy / kp.tile) * kp.nT + cz / kp.tile;
+        const int s = atomicAdd(tile_count + tile, 1);
+        if (s < cap) {
+            bucket[(size_t)tile * cap + s] = v;
+        } else {
+            const int o = atomicAdd(n_over, 1);
+            if (o < kp.N) over_idx[o] = i;
+        }
+        wrapped[i] = v;
         sq = df_add(sq, df_from((float)qq));
         sa = df_add(sa, df_from(fabsf((float)qq)));
         qmax = fmaxf(qmax, fabsf((float)qq));
@@ -93,7 +116,7 @@ k_fbin(const T* __restrict__ xyz, const T* __restrict__ q, const KParams<T> kp,
     const df2 r0 = block_sum_df(sq, sbuf);
     const df2 r1 = block_sum_df(sa, sbuf);
     if (threadIdx.x == 0) {
-        // per block: q sum (hi, lo), |q| sum (hi, lo), non-finite count
+        // per block: q sum (hi, lo), |q| sum (hi, lo), non-finite count, max |q|
         float* pf = reinterpret_cast<float*>(partials);
         pf[6 * blockIdx.x] = r0.hi;
         pf[6 * blockIdx.x + 1] = r0.lo;
@@ -152,68 +175,14 @@ __device__ __forceinline__ int fx_shift_for(double B) {
     return k < -60 ? -60 : (k > 100 ? 100 : k);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256)
-k_fscatter(const T* __restrict__ xyz, const T* __restrict__ q, const KParams<T> kp,
-           const int* __restrict__ tile_count, const int* __restrict__ slot,
-           const int* __restrict__ tile_of, int* __restrict__ tile_start,
-           v4_t<T>* __restrict__ sorted, int* __restrict__ perm,
-           const double* __restrict__ partials, int nbin_blocks, Acc* acc) {
-    SE_STAMP(1, 0);
-    pdl_wait();
-    pdl_launch_next();
-    SE_STAMP(1, 1);
-    __shared__ df2 sbuf[32];
-    __shared__ int s_start[kScanSmem + 1];
-    const int n = kp.ntiles;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) s_start[k] = tile_count[k];
-    __syncthreads();
-    block_scan_smem(s_start, n);
-    SE_STAMP(1, 2);
-    if (blockIdx.x == 0) {
-        for (int k = threadIdx.x; k < n; k += blockDim.x) tile_start[k] = s_start[k];
-        if (threadIdx.x == 0) tile_start[n] = kp.N;
-        const float* pf = reinterpret_cast<const float*>(partials);
-        const df2 a = sum_partials_df(pf, nbin_blocks, 3, 0, sbuf);
-        const df2 b = sum_partials_df(pf, nbin_blocks, 3, 1, sbuf);
-        int nbad = 0;
-        unsigned qm = 0u;
-        for (int k = threadIdx.x; k < nbin_blocks; k += blockDim.x) {
-            nbad += __float_as_int(__ldcg(pf + 6 * k + 4));
-            qm = max(qm, __float_as_uint(__ldcg(pf + 6 * k + 5)));
-        }
-        __shared__ int sb;
-        __shared__ unsigned sqm;
-        if (threadIdx.x == 0) {
-            sb = 0;
-            sqm = 0u;
-        }
-        __syncthreads();
-        if (nbad) atomicAdd(&sb, nbad);
-        atomicMax(&sqm, qm);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            acc->sum_q = df_to_double(a);
-            acc->sum_absq = df_to_double(b);
-            acc->nonfinite = (unsigned)sb;
-            const int k = fx_shift_for((double)kp.qcg * (double)__uint_as_float(sqm));
-            acc->fx_shift = k;
-            acc->fx_scale = ldexpf(1.0f, k);
-            acc->fx_inv = ldexpf(1.0f, -k);
-        }
-    }
-    SE_STAMP(1, 3);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kp.N; i += gridDim.x * blockDim.x) {
-        const int dst = s_start[tile_of[i]] + slot[i];
-        v4_t<T> v;
-        v.x = wrap_coord(xyz[3 * i], kp.L, kp.invL);
-        v.y = wrap_coord(xyz[3 * i + 1], kp.L, kp.invL);
-        v.z = wrap_coord(xyz[3 * i + 2], kp.L, kp.invL);
-        v.w = q[i];
-        sorted[dst] = v;
-        perm[dst] = i;
-    }
-    SE_STAMP(1, 4);
+// The same shift from a float bound, with integer operations only: for
+// B = m 2^e (m in [0.5, 1)), ceil(log2 B) is e, or e - 1 when m = 0.5.
+__device__ __forceinline__ int fx_shift_for_f(float B) {
+    if (!(B > 0.0f) || !isfinite(B)) return 40;
+    int e;
+    const float m = frexpf(B, &e);
+    const int k = 40 - (m == 0.5f ? e - 1 : e);
+    return k < -60 ? -60 : (k > 100 ? 100 : k);
 }
 
 // A scaled weight v (float, |v| < 2^62) rounded to the nearest integer and
@@ -269,18 +238,17 @@ __device__ __forceinline__ unsigned long long fx_join2(unsigned a0, unsigned a1)
     return ((unsigned long long)(long long)(int)a1 << 21) + (unsigned long long)a0;
 }
 
-// Spread of one tile (Eq. 3.5) into the fixed-point grid g64.  tile_start
-// holds the tile's particle range in `sorted`; fxs is the fixed-point scale.
-// Called by one whole block (uniformly: the early return is per block).
+// Spread of one tile (Eq. 3.5) into the fixed-point grid g64: the n
+// particles parts[0..n) of the tile; fxs is the fixed-point scale.  Called by
+// one whole block (uniformly: the early return is per block).
 template <int P>
-__device__ __forceinline__ void spread_tile(const f4* __restrict__ sorted,
-                                            const int* __restrict__ tile_start,
+__device__ __forceinline__ void spread_tile(const f4* __restrict__ parts, int n,
                                             unsigned long long* __restrict__ g64,
                                             const KParams<float>& kp, float fxs, int slab,
                                             int tile, unsigned* hi, float* sE3) {
     constexpr int D = pick_d(P), G = P / D, GPW = 32 / G;
-    const int pbeg = tile_start[tile], pend = tile_start[tile + 1];
-    if (pbeg == pend) return;
+    const int pbeg = 0, pend = n;
+    if (n <= 0) return;
     if (threadIdx.x < P) sE3[threadIdx.x] = kp.E3[threadIdx.x];
     const int nT = kp.nT, M = kp.M, TT = kp.tile;
     const int tz = tile % nT, ty = (tile / nT) % nT, tx = tile / (nT * nT);
@@ -309,7 +277,7 @@ __device__ __forceinline__ void spread_tile(const f4* __restrict__ sorted,
         SE_STAMP(2, 2);
         if (act) {
             for (int p = pbeg + group; p < pend; p += ngroups) {
-                const f4 v = sorted[p];
+                const f4 v = parts[p];
                 float t;
                 const int cx = cell_of(v.x, kp.invh, M, &t);
                 const float ux = centre_offset(t, cx);
@@ -372,22 +340,269 @@ __device__ __forceinline__ void spread_tile(const f4* __restrict__ sorted,
     }
 }
 
+// One particle's P^3 weights added straight into the fixed-point grid with
+// 64-bit integer atomics (the overflow path of the tile buckets), by the G
+// lanes of its group (lane k of the group: z points k, k + G, ...).
+template <int P>
+__device__ __forceinline__ void spread_particle_fx(const f4& v, unsigned long long* __restrict__ g64,
+                                                   const KParams<float>& kp, float fxs,
+                                                   const float* sE3, int k) {
+    constexpr int D = pick_d(P), G = P / D;
+    const int M = kp.M;
+    float t;
+    const int cx = cell_of(v.x, kp.invh, M, &t);
+    const float ux = centre_offset(t, cx);
+    const int cy = cell_of(v.y, kp.invh, M, &t);
+    const float uy = centre_offset(t, cy);
+    const int cz = cell_of(v.z, kp.invh, M, &t);
+    const float uz = centre_offset(t, cz);
+    float gy[P];
+    fgg<float, P>(uy, kp.beta, kp.E3, gy);
+    float gz[D];
+    int jz[D];
+    const float qw = v.w * kp.qcg * fxs;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const int c = k + j * G;
+        const float dz = float(c) - 0.5f * float(P - 1) - uz;
+        gz[j] = qw * expf(-kp.beta * dz * dz);
+        jz[j] = wrap_index(cz - P / 2 + 1 + c, M);
+    }
+    const float Bx = expf(2.0f * kp.beta * ux);
+    float px = expf(-kp.beta * ux * (ux + float(P - 1)));
+#pragma unroll 1
+    for (int a = 0; a < P; ++a) {
+        const float gxa = px * sE3[a];
+        px *= Bx;
+        const size_t plane = (size_t)wrap_index(cx - P / 2 + 1 + a, M) * M;
+#pragma unroll
+        for (int b = 0; b < P; ++b) {
+            const float wab = gxa * gy[b];
+            unsigned long long* row = g64 + (plane + wrap_index(cy - P / 2 + 1 + b, M)) * M;
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                unsigned vh, vl;
+                fx_split(wab * gz[j], &vh, &vl);
+                atomicAdd(row + jz[j], ((unsigned long long)vh << 32) | (unsigned long long)vl);
+            }
+        }
+    }
+}
+
+constexpr int kOverflowBlocks = 8;   // CTAs after the tile CTAs, for the overflow list
+
+// Spread (Eq. 3.5): CTA t < ntiles spreads tile t's bucket through shared
+// memory; the last kOverflowBlocks CTAs add the overflow list with global
+// atomics, and the last of them to finish clears the overflow count.  Every
+// CTA takes the fixed-point scale from the bin kernel's per-block max |q|;
+// CTA 0 also publishes the input checks and the scale for the transform.
 template <int P>
 __global__ void __launch_bounds__(256)
-k_fspread(const f4* __restrict__ sorted, const int* __restrict__ tile_start,
-          int* __restrict__ tile_count, unsigned long long* __restrict__ g64,
-          const KParams<float> kp, const Acc* __restrict__ acc, int slab) {
+k_fspread(const f4* __restrict__ bucket, int cap, int* __restrict__ tile_count,
+          const int* __restrict__ over_idx, int* __restrict__ n_over,
+          const f4* __restrict__ wrapped, unsigned long long* __restrict__ g64,
+          const KParams<float> kp, const double* __restrict__ partials, int nbin,
+          unsigned* ticket, Acc* __restrict__ acc, int slab) {
     SE_STAMP(2, 0);
     pdl_wait();
     pdl_launch_next();
     SE_STAMP(2, 1);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ float sE3[P];
-    // the counters are consumed: clear them for the next evaluation
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < kp.ntiles; k += gridDim.x * blockDim.x)
-        tile_count[k] = 0;
-    spread_tile<P>(sorted, tile_start, g64, kp, acc->fx_scale, slab, blockIdx.x,
-                   reinterpret_cast<unsigned*>(smem_raw), sE3);
+    __shared__ float s_fxs;
+    __shared__ int s_n;
+    __shared__ df2 sbuf[32];
+    __shared__ unsigned s_qm;
+    const float* pf = reinterpret_cast<const float*>(partials);
+    const int tile = blockIdx.x;
+    // one round trip: max |q| of the bin blocks, this CTA's particle count
+    if (threadIdx.x == 0) s_qm = 0u;
+    unsigned m = 0u;
+    for (int b = threadIdx.x; b < nbin; b += blockDim.x) m = max(m, __float_as_uint(__ldcg(pf + 6 * b + 5)));
+    int cnt = 0;
+    if (threadIdx.x == blockDim.x - 1) cnt = tile < kp.ntiles ? __ldcg(tile_count + tile) : __ldcg(n_over);
+    if (threadIdx.x < P) sE3[threadIdx.x] = kp.E3[threadIdx.x];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) atomicMax(&s_qm, m);
+    if (threadIdx.x == blockDim.x - 1) {
+        if (tile < kp.ntiles) {
+            s_n = min(cnt, cap);
+            tile_count[tile] = 0;   // consumed: clear for the next evaluation
+        } else {
+            s_n = min(cnt, kp.N);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int k = fx_shift_for_f(kp.qcg * __uint_as_float(s_qm));
+        s_fxs = ldexpf(1.0f, k);
+        if (blockIdx.x == 0) {
+            acc->fx_shift = k;
+            acc->fx_scale = ldexpf(1.0f, k);
+            acc->fx_inv = ldexpf(1.0f, -k);
+        }
+    }
+    __syncthreads();
+    if (blockIdx.x == 0) {
+        const df2 a = sum_partials_df(pf, nbin, 3, 0, sbuf);
+        const df2 b = sum_partials_df(pf, nbin, 3, 1, sbuf);
+        int nbad = 0;
+        for (int i = threadIdx.x; i < nbin; i += blockDim.x) nbad += __float_as_int(__ldcg(pf + 6 * i + 4));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nbad += __shfl_xor_sync(0xffffffffu, nbad, o);
+        __shared__ int sb;
+        if (threadIdx.x == 0) sb = 0;
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0 && nbad) atomicAdd(&sb, nbad);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            acc->sum_q = df_to_double(a);
+            acc->sum_absq = df_to_double(b);
+            acc->nonfinite = (unsigned)sb;
+        }
+    }
+    const float fxs = s_fxs;
+    const int n = s_n;
+    if (tile < kp.ntiles) {
+        spread_tile<P>(bucket + (size_t)tile * cap, n, g64, kp, fxs, slab, tile,
+                       reinterpret_cast<unsigned*>(smem_raw), sE3);
+        return;
+    }
+    constexpr int D = pick_d(P), G = P / D, GPW = 32 / G;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gi = lane / G, k = lane - gi * G;
+    const int ngroups = kOverflowBlocks * (blockDim.x >> 5) * GPW;
+    if (gi < GPW) {
+        for (int o = ((blockIdx.x - kp.ntiles) * (blockDim.x >> 5) + warp) * GPW + gi; o < n;
+             o += ngroups)
+            spread_particle_fx<P>(wrapped[over_idx[o]], g64, kp, fxs, sE3, k);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned t = atomicAdd(ticket, 1u);
+        if (t == kOverflowBlocks - 1) {   // every overflow CTA has read the count
+            *n_over = 0;
+            *ticket = 0u;
+        }
+    }
+}
+
+// Unsorted spread (Eq. 3.5) in one kernel: a group of G lanes takes one
+// particle (in input order) and adds its P^3 weights q c_g e^{-alpha r^2}
+// into the float grid with global reductions, so that the last bits of the
+// grid depend on the order in which the additions land.  The grid must be
+// zero on entry.  Also writes every particle's wrapped (x, y, z, q) for the
+// gather, and the input checks (q sums, non-finite count) through a
+// last-block reduction.
+template <int P>
+__global__ void __launch_bounds__(256)
+k_fdirect(const float* __restrict__ xyz, const float* __restrict__ q, const KParams<float> kp,
+          float* __restrict__ grid, f4* __restrict__ wrapped, double* __restrict__ partials,
+          unsigned* ticket, Acc* acc) {
+    constexpr int D = pick_d(P), G = P / D, GPW = 32 / G;
+    SE_STAMP(2, 0);
+    pdl_wait();
+    pdl_launch_next();
+    SE_STAMP(2, 1);
+    __shared__ float sE3[P];
+    __shared__ df2 sbuf[32];
+    __shared__ int sbad;
+    if (threadIdx.x < P) sE3[threadIdx.x] = kp.E3[threadIdx.x];
+    if (threadIdx.x == 0) sbad = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gi = lane / G, k = lane - gi * G;
+    const int gpb = (blockDim.x >> 5) * GPW;
+    const int M = kp.M;
+    df2 sq = df_from(0.0f), sa = df_from(0.0f);
+    int bad = 0;
+    // group g of CTA b takes particles b + gridDim.x g + (all groups) i: the
+    // particles of one CTA (and of one warp) lie far apart in the input order,
+    // so that neighbouring particles, whose weights land on the same grid
+    // points, do not queue on the same addresses at the same time
+    const int ngroups = gridDim.x * gpb;
+    for (int p = (warp * GPW + gi) * gridDim.x + blockIdx.x; gi < GPW && p < kp.N; p += ngroups) {
+        const float x = xyz[3 * p], y = xyz[3 * p + 1], z = xyz[3 * p + 2], qq = q[p];
+        f4 v;
+        v.x = wrap_coord(x, kp.L, kp.invL);
+        v.y = wrap_coord(y, kp.L, kp.invL);
+        v.z = wrap_coord(z, kp.L, kp.invL);
+        v.w = qq;
+        if (k == 0) {
+            wrapped[p] = v;
+            if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(qq))) bad += 1;
+            sq = df_add(sq, df_from(qq));
+            sa = df_add(sa, df_from(fabsf(qq)));
+        }
+        float t;
+        const int cx = cell_of(v.x, kp.invh, M, &t);
+        const float ux = centre_offset(t, cx);
+        const int cy = cell_of(v.y, kp.invh, M, &t);
+        const float uy = centre_offset(t, cy);
+        const int cz = cell_of(v.z, kp.invh, M, &t);
+        const float uz = centre_offset(t, cz);
+        float gy[P];
+        int jy[P];
+        fgg<float, P>(uy, kp.beta, kp.E3, gy);
+#pragma unroll
+        for (int b = 0; b < P; ++b) jy[b] = wrap_index(cy - P / 2 + 1 + b, M) * M;
+        float gz[D];
+        int jz[D];
+        const float qw = qq * kp.qcg;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            const int c = k + j * G;
+            const float dz = float(c) - 0.5f * float(P - 1) - uz;
+            gz[j] = qw * expf(-kp.beta * dz * dz);
+            jz[j] = wrap_index(cz - P / 2 + 1 + c, M);
+        }
+        const float Bx = expf(2.0f * kp.beta * ux);
+        float px = expf(-kp.beta * ux * (ux + float(P - 1)));
+#pragma unroll(P <= 8 ? P : 1)
+        for (int a = 0; a < P; ++a) {
+            const float gxa = px * sE3[a];
+            px *= Bx;
+            float* plane = grid + (size_t)wrap_index(cx - P / 2 + 1 + a, M) * M * M;
+#pragma unroll
+            for (int b = 0; b < P; ++b) {
+                const float wab = gxa * gy[b];
+                float* row = plane + jy[b];
+#pragma unroll
+                for (int j = 0; j < D; ++j) atomicAdd(row + jz[j], wab * gz[j]);
+            }
+        }
+    }
+    SE_STAMP(2, 2);
+    if (bad) atomicAdd(&sbad, bad);
+    const df2 r0 = block_sum_df(sq, sbuf);
+    const df2 r1 = block_sum_df(sa, sbuf);
+    float* pf = reinterpret_cast<float*>(partials);
+    if (threadIdx.x == 0) {
+        pf[6 * blockIdx.x] = r0.hi;
+        pf[6 * blockIdx.x + 1] = r0.lo;
+        pf[6 * blockIdx.x + 2] = r1.hi;
+        pf[6 * blockIdx.x + 3] = r1.lo;
+        pf[6 * blockIdx.x + 4] = __int_as_float(sbad);
+    }
+    if (!last_block(ticket)) return;
+    const df2 a = sum_partials_df(pf, gridDim.x, 3, 0, sbuf);
+    const df2 b = sum_partials_df(pf, gridDim.x, 3, 1, sbuf);
+    __syncthreads();
+    if (threadIdx.x == 0) sbad = 0;
+    __syncthreads();
+    int nbad = 0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) nbad += __float_as_int(__ldcg(pf + 6 * i + 4));
+    if (nbad) atomicAdd(&sbad, nbad);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        acc->sum_q = df_to_double(a);
+        acc->sum_absq = df_to_double(b);
+        acc->nonfinite = (unsigned)sbad;
+        *ticket = 0u;
+    }
+    SE_STAMP(2, 3);
 }
 
 // ---------------------------------------------------------------------------
@@ -416,9 +631,11 @@ __host__ __device__ inline size_t slab_smem_bytes(int M) {
     return (size_t)M * sizeof(float2) + slab_a_bytes(M) + Mh * SP * sizeof(float2);
 }
 
-// Forward 2-D transform (z real-to-complex, then y) of x-slab x.
-__device__ __forceinline__ void slab_fwd_body(const long long* __restrict__ g64,
-                                              float2* __restrict__ C,
+// Forward 2-D transform (z real-to-complex, then y) of x-slab x.  The input
+// is the fixed-point grid (long long, scaled by inv), or the float grid of
+// the unsorted spread (float), which is cleared after it is read.
+template <typename G>
+__device__ __forceinline__ void slab_fwd_body(G* __restrict__ grid, float2* __restrict__ C,
                                               const float2* __restrict__ tw_g, int M, float inv,
                                               int x, unsigned char* sm) {
     const int Mh = M / 2 + 1, SP = M + 1;
@@ -426,13 +643,30 @@ __device__ __forceinline__ void slab_fwd_body(const long long* __restrict__ g64,
     float* S = reinterpret_cast<float*>(sm + (size_t)M * sizeof(float2));
     float2* T = reinterpret_cast<float2*>(sm + (size_t)M * sizeof(float2) + slab_a_bytes(M));
     load_twiddles(tw, tw_g, M);
-    const long long* src = g64 + (size_t)x * M * M;
-    for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
-        const int y = e / M, z = e - y * M;
-        // int64 -> float through its two 32-bit words (no 64-bit conversion)
-        const unsigned long long u = (unsigned long long)src[e];
-        const float hi = (float)(int)(u >> 32), lo = (float)(unsigned)(u & 0xffffffffull);
-        S[y * SP + z] = fmaf(hi, 4294967296.0f, lo) * inv;
+    G* src = grid + (size_t)x * M * M;
+    // kLoadBatch loads per thread in flight before any is used
+    for (int e0 = threadIdx.x; e0 < M * M; e0 += blockDim.x * kLoadBatch) {
+        std::remove_const_t<G> v[kLoadBatch];
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int e = e0 + u * (int)blockDim.x;
+            v[u] = e < M * M ? src[e] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int e = e0 + u * (int)blockDim.x;
+            if (e >= M * M) break;
+            const int y = e / M, z = e - y * M;
+            if constexpr (sizeof(G) == sizeof(float)) {
+                S[y * SP + z] = v[u];
+                src[e] = 0.0f;
+            } else {
+                // int64 -> float through its two 32-bit words (no 64-bit conversion)
+                const unsigned long long w = (unsigned long long)v[u];
+                const float hi = (float)(int)(w >> 32), lo = (float)(unsigned)(w & 0xffffffffull);
+                S[y * SP + z] = fmaf(hi, 4294967296.0f, lo) * inv;
+            }
+        }
     }
     __syncthreads();
     SE_STAMP(3, 2);
@@ -456,6 +690,18 @@ k_slab_fwd(const long long* __restrict__ g64, float2* __restrict__ C,
     extern __shared__ __align__(16) unsigned char sm[];
     slab_fwd_body(g64, C, tw_g, M, acc->fx_inv, blockIdx.x, sm);
 }
+
+// the same on the float grid of the unsorted spread (cleared after reading)
+__global__ void __launch_bounds__(kSlabThreads)
+k_slab_fwd_f(float* __restrict__ grid, float2* __restrict__ C, const float2* __restrict__ tw_g,
+             int M) {
+    SE_STAMP(3, 0);
+    pdl_wait();
+    pdl_launch_next();
+    SE_STAMP(3, 1);
+    extern __shared__ __align__(16) unsigned char sm[];
+    slab_fwd_body(grid, C, tw_g, M, 1.0f, blockIdx.x, sm);
+}
 #endif  // SE_BATCH_TU
 
 // x pass of work item `item` = (ky, kz chunk): forward DFT along x, scaling
@@ -472,9 +718,24 @@ __device__ __forceinline__ df2 xpass_body(float2* __restrict__ C, const float2* 
     const int y = item / nch, c0 = (item % nch) * kFastKC;
     const int nc = min(kFastKC, Mh - c0);
     load_twiddles(tw, tw_g, M);
-    for (int e = threadIdx.x; e < M * nc; e += blockDim.x) {
-        const int x = e / nc, kk = e - x * nc;
-        s[x * kFastKC + kk] = C[((size_t)x * M + y) * Mh + c0 + kk];
+    for (int e0 = threadIdx.x; e0 < M * nc; e0 += blockDim.x * kLoadBatch) {
+        float2 v[kLoadBatch];
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int e = e0 + u * (int)blockDim.x;
+            if (e < M * nc) {
+                const int x = e / nc, kk = e - x * nc;
+                v[u] = C[((size_t)x * M + y) * Mh + c0 + kk];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int e = e0 + u * (int)blockDim.x;
+            if (e < M * nc) {
+                const int x = e / nc, kk = e - x * nc;
+                s[x * kFastKC + kk] = v[u];
+            }
+        }
     }
     __syncthreads();
     SE_STAMP(4, 2);
@@ -538,7 +799,19 @@ __device__ __forceinline__ void slab_inv_body(const float2* __restrict__ C, floa
     float2* T = reinterpret_cast<float2*>(sm + (size_t)M * sizeof(float2) + slab_a_bytes(M));
     load_twiddles(tw, tw_g, M);
     const float2* src = C + (size_t)x * M * Mh;
-    for (int e = threadIdx.x; e < M * Mh; e += blockDim.x) A[e] = src[e];
+    for (int e0 = threadIdx.x; e0 < M * Mh; e0 += blockDim.x * kLoadBatch) {
+        float2 v[kLoadBatch];
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int e = e0 + u * (int)blockDim.x;
+            if (e < M * Mh) v[u] = src[e];
+        }
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int e = e0 + u * (int)blockDim.x;
+            if (e < M * Mh) A[e] = v[u];
+        }
+    }
     __syncthreads();
     // y inverse: X(j = ky, c = kz) = A[ky][kz]  ->  T[kz][y], with the
     // Hermitian weights of the z real transform (1 at kz = 0 and M/2, else 2)

@@ -17,7 +17,7 @@ inline int fast_bin_blocks(const KParams<float>& kp) {
 }
 
 template <int P>
-cudaError_t fast_spread_P(const KParams<float>& kp, const FastBufs& b, cudaStream_t s) {
+cudaError_t fast_spread_P(const KParams<float>& kp, const FastBufs& b, int nbin, cudaStream_t s) {
     const size_t R = (size_t)kp.tile + P - 1;
     const size_t plane = R * R * 2 * sizeof(unsigned);
     const int slab = (int)std::min(R, kSmemBudget / plane);
@@ -25,24 +25,50 @@ cudaError_t fast_spread_P(const KParams<float>& kp, const FastBufs& b, cudaStrea
     cudaError_t e = cudaFuncSetAttribute(k_fspread<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kSmemBudget);
     if (e != cudaSuccess) return e;
-    return launch_ex(k_fspread<P>, kp.ntiles, kThreads, (size_t)slab * plane, s, true,
-                     (const f4*)b.sorted, (const int*)b.tile_start, b.tile_count,
-                     (unsigned long long*)b.g64, kp, (const Acc*)b.acc, slab);
+    // an ordinary launch (no early scheduling): the CTAs are then spread over
+    // all SMs instead of being packed onto the SMs that had room during the bin
+    return launch_ex(k_fspread<P>, kp.ntiles + kOverflowBlocks, kThreads, (size_t)slab * plane, s,
+                     false, (const f4*)b.bucket, b.cap, b.tile_count, (const int*)b.over_idx,
+                     (int*)(b.tickets + 4), (const f4*)b.wrapped, (unsigned long long*)b.g64, kp,
+                     (const double*)b.partials, nbin, b.tickets + 3, b.acc, slab);
+}
+
+template <int P>
+cudaError_t fast_direct_P(const float* xyz, const float* q, const KParams<float>& kp,
+                          const FastBufs& b, cudaStream_t s) {
+    constexpr int GPW = 32 / (P / pick_d(P));
+    const int gpb = (kThreads / 32) * GPW;
+    const int blocks = std::max(1, std::min((kp.N + gpb - 1) / gpb, kMaxPartials));
+    return launch_ex(k_fdirect<P>, blocks, kThreads, 0, s, false, xyz, q, kp, (float*)b.g64,
+                     (f4*)b.wrapped, b.partials, b.tickets + 0, b.acc);
 }
 
 cudaError_t fast_spread(const float* xyz, const float* q, const KParams<float>& kp,
-                        const FastBufs& b, cudaStream_t s) {
+                        const FastBufs& b, cudaStream_t s, bool marks, void (*mark)(void*, int),
+                        void* ctx) {
+    if (b.unsorted) {
+        if (marks) {
+            mark(ctx, 0);
+            mark(ctx, 1);
+        }
+        switch (kp.P) {
+#define SE_CASE(PP) case PP: return fast_direct_P<PP>(xyz, q, kp, b, s);
+            SE_FOR_EACH_P(SE_CASE)
+#undef SE_CASE
+            default: return cudaErrorInvalidValue;
+        }
+    }
     const int nbin = fast_bin_blocks(kp);
     cudaError_t e = launch_ex(k_fbin<float>, nbin, kThreads, 0, s, false, xyz, q, kp, b.tile_count,
-                              b.slot, b.tile_of, b.partials, b.g64);
+                              (f4*)b.bucket, b.cap, b.over_idx, (int*)(b.tickets + 4),
+                              (f4*)b.wrapped, b.partials, b.g64);
     if (e != cudaSuccess) return e;
-    const int nsc = std::max(1, std::min((kp.N + kThreads - 1) / kThreads, 160));
-    e = launch_ex(k_fscatter<float>, nsc, kThreads, 0, s, true, xyz, q, kp,
-                  (const int*)b.tile_count, (const int*)b.slot, (const int*)b.tile_of, b.tile_start,
-                  (f4*)b.sorted, b.perm, (const double*)b.partials, nbin, b.acc);
-    if (e != cudaSuccess) return e;
+    if (marks) {
+        mark(ctx, 0);
+        mark(ctx, 1);
+    }
     switch (kp.P) {
-#define SE_CASE(PP) case PP: return fast_spread_P<PP>(kp, b, s);
+#define SE_CASE(PP) case PP: return fast_spread_P<PP>(kp, b, nbin, s);
         SE_FOR_EACH_P(SE_CASE)
 #undef SE_CASE
         default: return cudaErrorInvalidValue;
@@ -56,13 +82,21 @@ cudaError_t fast_transform(const KParams<float>& kp, const FastBufs& b, double e
     const int nch = (Mh + kFastKC - 1) / kFastKC;
     const float2* tw = (const float2*)b.tw;
     float2* C = (float2*)b.cgrid;
-    const size_t slab = slab_smem_bytes(M);
+    // at least half an SM's shared memory: one slab CTA per SM, whatever else
+    // is resident when the grid is scheduled early
+    const size_t slab = std::max(slab_smem_bytes(M), kSlabSmemFloor);
     cudaError_t e = cudaFuncSetAttribute(k_slab_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_slab_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab);
     if (e != cudaSuccess) return e;
-    e = launch_ex(k_slab_fwd, M, kSlabThreads, slab, s, true, (const long long*)b.g64, C, tw, M,
-                  (const Acc*)b.acc);
+    if (b.unsorted) {
+        e = cudaFuncSetAttribute(k_slab_fwd_f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab);
+        if (e != cudaSuccess) return e;
+        e = launch_ex(k_slab_fwd_f, M, kSlabThreads, slab, s, true, (float*)b.g64, C, tw, M);
+    } else {
+        e = launch_ex(k_slab_fwd, M, kSlabThreads, slab, s, true, (const long long*)b.g64, C, tw,
+                      M, (const Acc*)b.acc);
+    }
     if (e != cudaSuccess) return e;
     if (marks) mark(ctx, 3);
     const float invM3 = (float)(1.0 / ((double)M * M * M));

@@ -77,24 +77,26 @@ int make_kparams_f64(int64_t N, double L, double xi, int M, int P, int tile, KPa
 
 // single-precision pipeline without cuFFT (se_fast.cuh)
 struct FastBufs {
-    long long* g64;       // M^3 fixed-point spread grid
+    long long* g64;       // M^3 fixed-point spread grid (the float grid when unsorted)
     void* cgrid;          // M x M x (M/2+1) float2
     float* rgrid;         // M^3 real grid after the inverse transform
     const void* tw;       // M twiddles (cos, sin)(2 pi r / M), float2
     const double* green;  // G(k) on the half spectrum
     const float* green_f; // the same table rounded to float
     int* tile_count;
-    int* tile_start;
-    int* slot;
-    int* tile_of;
-    int* perm;
-    void* sorted;         // f4 [N]
+    void* bucket;         // f4 [ntiles * cap]: particles by tile
+    int cap;              // bucket capacity
+    int* over_idx;        // [N] particles that found their bucket full
+    void* wrapped;        // f4 [N]: wrapped (x, y, z, q) in input order, for the gather
     double* partials;     // bin: [0, 3*1024); x pass: [5*1024, 7*1024)
-    unsigned* tickets;
+    unsigned* tickets;    // [0] unsorted spread, [1] x pass, [2] gather, [3] overflow
+                          // CTAs, [4] overflow count
     Acc* acc;
+    bool unsorted;        // spread unsorted into a float grid (k_fdirect)
 };
 cudaError_t fast_spread(const float* xyz, const float* q, const KParams<float>& kp,
-                        const FastBufs& b, cudaStream_t s);
+                        const FastBufs& b, cudaStream_t s, bool marks, void (*mark)(void*, int),
+                        void* ctx);
 cudaError_t fast_transform(const KParams<float>& kp, const FastBufs& b, double e_scale,
                            double* E_grid, cudaStream_t s, bool marks, void (*mark)(void*, int),
                            void* ctx);
@@ -108,5 +110,6 @@ constexpr int kMaxPartials = 1024;   // blocks of the reducing kernels
 constexpr int kFastMaxM = 128;       // largest grid of the single-precision pipeline
 constexpr int kScanLimit = 8192;     // tiles scanned in shared memory
 constexpr size_t kSmemBudget = 200 * 1024;  // dynamic shared memory for a spreading tile
+constexpr size_t kSlabSmemFloor = 116 * 1024;  // > half of an SM's 228 KB: one slab CTA per SM
 
 }  // namespace se

@@ -102,6 +102,11 @@ __device__ unsigned long long se_trace_buf[kTraceKernels][kTraceBlocks][kTracePh
             unsigned long long t_;                                                          \
             asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_));                          \
             se_trace_buf[kid][blockIdx.x][ph] = t_;                                         \
+            if ((ph) == 0) {                                                                \
+                unsigned sm_;                                                               \
+                asm volatile("mov.u32 %0, %%smid;" : "=r"(sm_));                            \
+                se_trace_buf[kid][blockIdx.x][kTracePhases - 1] = sm_;                      \
+            }                                                                               \
         }                                                                                   \
     } while (0)
 #else
@@ -561,64 +566,81 @@ k_scale(C* __restrict__ cgrid, const double* __restrict__ green, int M, double i
 // reduced per block and finished by the last block.
 // ---------------------------------------------------------------------------
 // Potential and force sums of one particle on the grid (Eq. 3.9 and the
-// analytic force of Sec. 3.1), for this lane's z points: returns the partial
-// sums vphi, vfx, vfy, vfz (to be reduced over the particle's G lanes).
+// analytic force of Sec. 3.1), in two parts: gather_prep computes the
+// particle's separable Gaussian factors and grid indices (no grid access, so
+// it may run before the grid is ready), gather_accum the sums over this
+// lane's z points, vphi, vfx, vfy, vfz (to be reduced over the particle's G
+// lanes).
 template <typename T, int P>
-__device__ __forceinline__ void gather_particle(const v4_t<T>& v, const T* __restrict__ grid,
-                                                const KParams<T>& kp, const T* sE3, int k, T& vphi,
-                                                T& vfx, T& vfy, T& vfz) {
+struct GatherPrep {
+    static constexpr int D = pick_d(P);
+    T gy[P], dgy[P], gz[D], dgz[D];
+    int jy[P], jz[D];
+    T ux, px0, Bx;
+    int i0x;
+};
+
+template <typename T, int P>
+__device__ __forceinline__ void gather_prep(const v4_t<T>& v, const KParams<T>& kp, int k,
+                                            GatherPrep<T, P>& g) {
     constexpr int D = pick_d(P), G = P / D;
     const int M = kp.M;
     T t;
     const int cx = cell_of(v.x, kp.invh, M, &t);
-    const T ux = centre_offset(t, cx);
+    g.ux = centre_offset(t, cx);
     const int cy = cell_of(v.y, kp.invh, M, &t);
     const T uy = centre_offset(t, cy);
     const int cz = cell_of(v.z, kp.invh, M, &t);
     const T uz = centre_offset(t, cz);
-    T gy[P], dgy[P];
-    int jy[P];
-    fgg<T, P>(uy, kp.beta, kp.E3, gy);
-    const int i0x = cx - P / 2 + 1, i0y = cy - P / 2 + 1;
+    fgg<T, P>(uy, kp.beta, kp.E3, g.gy);
+    g.i0x = cx - P / 2 + 1;
+    const int i0y = cy - P / 2 + 1;
 #pragma unroll
     for (int b = 0; b < P; ++b) {
-        dgy[b] = (T(b) - T(0.5) * T(P - 1) - uy) * gy[b];
-        jy[b] = wrap_index(i0y + b, M);
+        g.dgy[b] = (T(b) - T(0.5) * T(P - 1) - uy) * g.gy[b];
+        g.jy[b] = wrap_index(i0y + b, M);
     }
-    T gz[D], dgz[D];
-    int jz[D];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
         const int c = k + j * G;
         const T dz = T(c) - T(0.5) * T(P - 1) - uz;
-        gz[j] = expT(-kp.beta * dz * dz);
-        dgz[j] = dz * gz[j];
-        jz[j] = wrap_index(cz - P / 2 + 1 + c, M);
+        g.gz[j] = expT(-kp.beta * dz * dz);
+        g.dgz[j] = dz * g.gz[j];
+        g.jz[j] = wrap_index(cz - P / 2 + 1 + c, M);
     }
+    g.Bx = expT(T(2) * kp.beta * g.ux);
+    g.px0 = expT(-kp.beta * g.ux * (g.ux + T(P - 1)));
+}
+
+template <typename T, int P>
+__device__ __forceinline__ void gather_accum(const GatherPrep<T, P>& g, const T* __restrict__ grid,
+                                             const KParams<T>& kp, const T* sE3, T& vphi, T& vfx,
+                                             T& vfy, T& vfz) {
+    constexpr int D = pick_d(P);
+    const int M = kp.M;
     T acc0[D], accx[D], accy[D];
 #pragma unroll
     for (int j = 0; j < D; ++j) acc0[j] = accx[j] = accy[j] = T(0);
-    const T Bx = expT(T(2) * kp.beta * ux);
-    T px = expT(-kp.beta * ux * (ux + T(P - 1)));
+    T px = g.px0;
     // small supports: the whole x loop unrolled, so that every load of
     // the particle's P^3 grid values is in flight at once
 #pragma unroll(P <= 8 ? P : 1)
     for (int a = 0; a < P; ++a) {
         const T gxa = px * sE3[a];
-        const T dgxa = (T(a) - T(0.5) * T(P - 1) - ux) * gxa;
-        px *= Bx;
-        const int jx = wrap_index(i0x + a, M);
+        const T dgxa = (T(a) - T(0.5) * T(P - 1) - g.ux) * gxa;
+        px *= g.Bx;
+        const int jx = wrap_index(g.i0x + a, M);
         T tb0[D], tby[D];
 #pragma unroll
         for (int j = 0; j < D; ++j) tb0[j] = tby[j] = T(0);
 #pragma unroll
         for (int b = 0; b < P; ++b) {
-            const T* row = grid + ((size_t)jx * M + jy[b]) * M;
+            const T* row = grid + ((size_t)jx * M + g.jy[b]) * M;
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                const T hv = __ldg(row + jz[j]);
-                tb0[j] += gy[b] * hv;
-                tby[j] += dgy[b] * hv;
+                const T hv = __ldg(row + g.jz[j]);
+                tb0[j] += g.gy[b] * hv;
+                tby[j] += g.dgy[b] * hv;
             }
         }
 #pragma unroll
@@ -630,15 +652,17 @@ __device__ __forceinline__ void gather_particle(const v4_t<T>& v, const T* __res
     }
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-        vphi += gz[j] * acc0[j];
-        vfx += gz[j] * accx[j];
-        vfy += gz[j] * accy[j];
-        vfz += dgz[j] * acc0[j];
+        vphi += g.gz[j] * acc0[j];
+        vfx += g.gz[j] * accx[j];
+        vfy += g.gz[j] * accy[j];
+        vfz += g.dgz[j] * acc0[j];
     }
 }
 
+// Single precision and P <= 8: at most 64 registers, so that four CTAs fit on
+// an SM and a gather of up to 4 x 152 CTAs runs in one wave.
 template <typename T, int P>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 8) ? 4 : 1)
 k_gather(const v4_t<T>* __restrict__ sorted, const int* __restrict__ perm,
  const T* __restrict__ grid, T* __restrict__ phi, T* __restrict__ F,
  const KParams<T> kp, double* __restrict__ partials, unsigned* ticket, Acc* acc,
@@ -646,31 +670,44 @@ k_gather(const v4_t<T>* __restrict__ sorted, const int* __restrict__ perm,
     constexpr int D = pick_d(P), G = P / D, GPW = 32 / G;
     constexpr bool kSingle = sizeof(T) == sizeof(float);
     SE_STAMP(6, 0);
-    pdl_wait();
-    SE_STAMP(6, 1);
     __shared__ double sbuf[32];
     __shared__ df2 sbuf_df[32];
     __shared__ T sE3[P];
     if (threadIdx.x < P) sE3[threadIdx.x] = kp.E3[threadIdx.x];
-    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gi = lane / G, k = lane - gi * G;
     const int gpb = (blockDim.x >> 5) * GPW;
-    const int M = kp.M;
+    // the particles were written before the grid's transforms began: the
+    // first particle's factors are computed while the grid is still being
+    // produced (before the dependent-launch wait)
+    int pb = blockIdx.x * gpb + warp * GPW;
+    GatherPrep<T, P> g;
+    T qq = T(0);
+    if (gi < GPW && pb + gi < kp.N) {
+        const v4_t<T> v = sorted[pb + gi];
+        qq = v.w;
+        gather_prep<T, P>(v, kp, k, g);
+    }
+    pdl_wait();
+    SE_STAMP(6, 1);
+    __syncthreads();
     // adjoint (backward) mode: outputs are dl/dq = g phi and dl/dx = -g F for
     // the upstream gradient g = dl/dE read from device memory
     const T gsc = adj ? (T)__ldg(adj) : T(1);
     const T phi_mul = gsc, F_mul = adj ? -gsc : T(1);
     double e_loc = 0.0;
     df2 e_df = df_from(0.0f);
-    for (int pb = blockIdx.x * gpb + warp * GPW; pb < kp.N; pb += gridDim.x * gpb) {
+    for (; pb < kp.N; pb += gridDim.x * gpb) {
 const int p = pb + gi;
 const bool valid = (gi < GPW) && (p < kp.N);
-T vphi = T(0), vfx = T(0), vfy = T(0), vfz = T(0), qq = T(0);
+T vphi = T(0), vfx = T(0), vfy = T(0), vfz = T(0);
 if (valid) {
-    const v4_t<T> v = sorted[p];
-    qq = v.w;
-    gather_particle<T, P>(v, grid, kp, sE3, k, vphi, vfx, vfy, vfz);
+    if (pb != blockIdx.x * gpb + warp * GPW) {   // later particles: after the wait
+        const v4_t<T> v = sorted[p];
+        qq = v.w;
+        gather_prep<T, P>(v, kp, k, g);
+    }
+    gather_accum<T, P>(g, grid, kp, sE3, vphi, vfx, vfy, vfz);
 }
 SE_STAMP(6, 2);
 // reduce over the G lanes of each particle (lane 0 of the group ends with the sum)
@@ -690,7 +727,7 @@ for (int o = 1; o < G; o <<= 1) {
 if (valid && k == 0) {
     const T ph = vphi * kp.phi_scale;
     const T fs = qq * kp.F_scale;
-    const int orig = perm[p];
+    const int orig = perm ? perm[p] : p;   // no perm: particles in input order
     if (phi) phi[orig] = ph * phi_mul;
     if (F) {
         const T fm = fs * F_mul;

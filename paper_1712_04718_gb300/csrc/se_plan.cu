@@ -1,7 +1,8 @@
 // se_plan.cu -- libse host side: plans, device buffers, cuFFT plans and the
 // C ABI declared in include/se.h.
 //
-// One evaluation (se_energy_force) enqueues, on the plan's stream:
+// One evaluation (se_energy_force) enqueues, on the plan's stream, either the
+// cuFFT pipeline (spread variants 1 and 2: FP64, or grids above 128^3):
 //   k_bin (tile of each particle, slots, checks, tile offsets)
 //   k_scatter (particles in tile order)
 //   k_spread_{tiled,direct} (Eq. 3.5)
@@ -9,13 +10,17 @@
 //   k_scale (Eq. 3.6, grid energy; clears the spread grid for the next call)
 //   cuFFT C2R
 //   k_gather (Eq. 3.9 and the analytic force; energy 1/2 sum q phi)
-// and nothing else: no allocation, no memset, no host synchronisation except
-// the final copy of the energy when the caller asks for it on the host.
+// or the single-precision pipeline of se_fast.cuh (variant 3: k_fbin,
+// k_fspread, k_slab_fwd, k_xpass, k_slab_inv, k_gather; variant 4: k_fdirect
+// in place of the first two), and nothing else: no allocation, no memset, no
+// host synchronisation except the final copy of the energy when the caller
+// asks for it on the host.
 #include <cufft.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -40,6 +45,7 @@ struct se_plan {
     // derived (set by derive())
     double h = 0, w = 0, eta = 0, alpha = 0, cg = 0, m = 0;
     int tile = 0, nT = 0, ntiles = 0, variant = 0;
+    int cap = 0;                   // tile bucket capacity (single-precision pipeline)
 
     // device state (prepare())
     bool ready = false;
@@ -55,11 +61,12 @@ struct se_plan {
     int* tile_of = nullptr;
     int* perm = nullptr;
     void* sorted = nullptr;
+    void* bucket = nullptr;        // tile buckets (single-precision pipeline)
     long long* g64 = nullptr;      // fixed-point spread grid (single-precision pipeline)
     float* green_f = nullptr;      // G(k) table in float (single-precision pipeline)
     void* tw = nullptr;            // twiddles of the single-precision pipeline
     double* partials = nullptr;    // 8 x kMaxPartials
-    unsigned* tickets = nullptr;   // bin, scale, gather
+    unsigned* tickets = nullptr;   // 8 counters (see FastBufs)
     Acc* acc = nullptr;
     double* dE = nullptr;          // device energy for se_energy_force
     cufftHandle fwd = 0, inv = 0;
@@ -160,15 +167,20 @@ void derive(se_plan* p) {
     p->tile = tile;
     p->nT = (p->M + tile - 1) / tile;
     p->ntiles = p->nT * p->nT * p->nT;
-    const bool fast_ok = p->prec != SE_FP64 && p->M <= se::kFastMaxM && p->ntiles <= se::kScanLimit;
+    const bool fast_ok = p->prec != SE_FP64 && p->M <= se::kFastMaxM;
     int variant = p->tune_variant;
     if (variant == 3 && !fast_ok) variant = 0;
+    if (variant == 4 && (p->prec == SE_FP64 || p->M > se::kFastMaxM)) variant = 0;
     if (variant == 0) {
         if (p->prec == SE_FP64) variant = p->P > 12 ? 2 : 1;
         else variant = fast_ok ? 3 : 1;
     }
     if (p->prec == SE_FP32 && variant == 2) variant = 1;  // the compensated sum needs the tiles
     p->variant = variant;
+    // bucket capacity: twice the mean tile occupancy plus a margin; fuller
+    // tiles spill to the overflow list
+    const int64_t mean = (p->N + p->ntiles - 1) / std::max(1, p->ntiles);
+    p->cap = (int)std::min<int64_t>(std::max<int64_t>(32, 2 * mean + 32), std::max<int64_t>(32, p->N));
 }
 
 void drop_graph(se_plan* p) {
@@ -185,10 +197,11 @@ void release_device(se_plan* p) {
     }
     void* bufs[] = {p->grid_spread, p->grid_gather, p->cgrid, p->green, p->tile_count,
                     p->tile_start, p->slot, p->tile_of, p->perm, p->sorted, p->partials,
-                    p->tickets, p->acc, p->dE, p->h_xyz, p->h_q, p->h_F, p->h_phi, p->g64, p->tw, p->green_f};
+                    p->tickets, p->acc, p->dE, p->h_xyz, p->h_q, p->h_F, p->h_phi, p->g64, p->tw, p->green_f,
+                    p->bucket};
     for (void* b : bufs)
         if (b) cudaFree(b);
-    p->grid_spread = p->grid_gather = p->cgrid = p->sorted = p->tw = nullptr;
+    p->grid_spread = p->grid_gather = p->cgrid = p->sorted = p->tw = p->bucket = nullptr;
     p->g64 = nullptr;
     p->green_f = nullptr;
     p->green = p->partials = p->dE = nullptr;
@@ -265,10 +278,12 @@ int prepare(se_plan* p) {
     const size_t M3 = (size_t)p->M * p->M * p->M;
     const size_t nc = (size_t)p->M * p->M * (p->M / 2 + 1);
     const size_t N = (size_t)p->N;
-    const bool fast = p->variant == 3;
+    const bool fast = p->variant >= 3;
     int rc = SE_OK;
     if (rc == SE_OK && !fast) rc = dalloc(&p->grid_spread, M3 * ts);
     if (rc == SE_OK && fast) rc = dalloc((void**)&p->g64, M3 * sizeof(long long));
+    if (rc == SE_OK && p->variant == 3)
+        rc = dalloc(&p->bucket, (size_t)p->ntiles * p->cap * 4 * sizeof(float));
     if (rc == SE_OK && fast) rc = dalloc(&p->tw, (size_t)p->M * 2 * sizeof(float));
     if (rc == SE_OK && fast) rc = dalloc((void**)&p->green_f, nc * sizeof(float));
     if (rc == SE_OK) rc = dalloc(&p->grid_gather, M3 * ts);
@@ -281,7 +296,7 @@ int prepare(se_plan* p) {
     if (rc == SE_OK) rc = dalloc((void**)&p->perm, N * sizeof(int));
     if (rc == SE_OK) rc = dalloc(&p->sorted, N * 4 * ts);
     if (rc == SE_OK) rc = dalloc((void**)&p->partials, 8 * se::kMaxPartials * sizeof(double));
-    if (rc == SE_OK) rc = dalloc((void**)&p->tickets, 4 * sizeof(unsigned));
+    if (rc == SE_OK) rc = dalloc((void**)&p->tickets, 8 * sizeof(unsigned));
     if (rc == SE_OK) rc = dalloc((void**)&p->acc, sizeof(Acc));
     if (rc == SE_OK) rc = dalloc((void**)&p->dE, sizeof(double));
     if (rc != SE_OK) {
@@ -291,9 +306,10 @@ int prepare(se_plan* p) {
     std::vector<double> g = green_table(p);
     if (cudaMemcpy(p->green, g.data(), nc * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(p->tile_count, 0, (size_t)p->ntiles * sizeof(int)) != cudaSuccess ||
-        cudaMemset(p->tickets, 0, 4 * sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(p->tickets, 0, 8 * sizeof(unsigned)) != cudaSuccess ||
         cudaMemset(p->acc, 0, sizeof(Acc)) != cudaSuccess ||
-        (!fast && cudaMemset(p->grid_spread, 0, M3 * ts) != cudaSuccess)) {
+        (!fast && cudaMemset(p->grid_spread, 0, M3 * ts) != cudaSuccess) ||
+        (p->variant == 4 && cudaMemset(p->g64, 0, M3 * sizeof(float)) != cudaSuccess)) {
         release_device(p);
         return SE_ERR_CUDA;
     }
@@ -359,26 +375,30 @@ se::FastBufs fast_bufs(se_plan* p) {
     b.green = p->green;
     b.green_f = p->green_f;
     b.tile_count = p->tile_count;
-    b.tile_start = p->tile_start;
-    b.slot = p->slot;
-    b.tile_of = p->tile_of;
-    b.perm = p->perm;
-    b.sorted = p->sorted;
+    b.bucket = p->bucket;
+    b.cap = p->cap;
+    b.over_idx = p->slot;
+    b.wrapped = p->sorted;
     b.partials = p->partials;
     b.tickets = p->tickets;
     b.acc = p->acc;
+    b.unsorted = p->variant == 4;
     return b;
 }
 
 void mark_cb(void* ctx, int s) { timing_mark(static_cast<se_plan*>(ctx), s); }
 
+
 int fast_spread(se_plan* p, const void* xyz, const void* q) {
     const KParams<float> kp = make_kparams<float>(p);
+    // the unsorted spread adds into the float grid, which k_slab_fwd_f clears
+    if (p->variant == 4 && !p->spread_clean)
+        SE_CUDA(cudaMemsetAsync(p->g64, 0, (size_t)p->M * p->M * p->M * sizeof(float), p->stream));
     timing_begin(p);
-    SE_CUDA(se::fast_spread((const float*)xyz, (const float*)q, kp, fast_bufs(p), p->stream));
-    timing_mark(p, 0);
-    timing_mark(p, 1);
+    SE_CUDA(se::fast_spread((const float*)xyz, (const float*)q, kp, fast_bufs(p), p->stream,
+                            p->ev_cur >= 0, mark_cb, p));
     timing_mark(p, 2);
+    p->spread_clean = p->variant != 4;
     p->have_spread = true;
     p->have_scale = false;
     return SE_OK;
@@ -390,13 +410,14 @@ int fast_scale(se_plan* p, double* E_grid) {
     const double e_scale = p->kc * p->h * p->h * p->h / (2.0 * M3);
     SE_CUDA(se::fast_transform(kp, fast_bufs(p), e_scale, E_grid, p->stream, p->ev_cur >= 0,
                                mark_cb, p));
+    p->spread_clean = true;
     p->have_scale = true;
     return SE_OK;
 }
 
 int fast_gather(se_plan* p, void* phi, void* F, double* E, const double* adj = nullptr) {
     const KParams<float> kp = make_kparams<float>(p);
-    SE_CUDA(se::launch_gather_pdl((const se::f4*)p->sorted, p->perm, (const float*)p->grid_gather,
+    SE_CUDA(se::launch_gather_pdl((const se::f4*)p->sorted, nullptr, (const float*)p->grid_gather,
                                   (float*)phi, (float*)F, kp, p->partials + 4 * se::kMaxPartials,
                                   p->tickets + 2, p->acc, 0.5, E, adj, p->stream));
     timing_mark(p, 6);
@@ -472,7 +493,7 @@ int status_from_acc(const Acc& a) {
 }
 
 int evaluate(se_plan* p, const void* xyz, const void* q, void* F, void* phi, double* dE) {
-    if (p->variant == 3) {
+    if (p->variant >= 3) {
         SE_TRY(fast_spread(p, xyz, q));
         SE_TRY(fast_scale(p, nullptr));
         SE_TRY(fast_gather(p, phi, F, dE));
@@ -507,7 +528,10 @@ int graph_evaluate(se_plan* p, const void* xyz, const void* q, void* F, void* ph
             SE_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
         if (!p->spread_clean && p->variant != 3) {
             const size_t M3 = (size_t)p->M * p->M * p->M;
-            SE_CUDA(cudaMemsetAsync(p->grid_spread, 0, M3 * tsize(p->prec), p->stream));
+            if (p->variant == 4)
+                SE_CUDA(cudaMemsetAsync(p->g64, 0, M3 * sizeof(float), p->stream));
+            else
+                SE_CUDA(cudaMemsetAsync(p->grid_spread, 0, M3 * tsize(p->prec), p->stream));
             p->spread_clean = true;
         }
         // the capture stream must see the state the user stream has reached
@@ -669,9 +693,9 @@ int se_plan_set_stream(se_plan* p, void* stream) {
 }
 
 int se_plan_set_tuning(se_plan* p, int spread_variant, int tile) {
-    if (!p || spread_variant < 0 || spread_variant > 3 || (tile != 0 && (tile < 2 || tile > 32)))
+    if (!p || spread_variant < 0 || spread_variant > 4 || (tile != 0 && (tile < 2 || tile > 32)))
         return SE_ERR_ARG;
-    if (spread_variant == 3 && (p->prec == SE_FP64 || p->M > se::kFastMaxM)) return SE_ERR_UNSUPPORTED;
+    if (spread_variant >= 3 && (p->prec == SE_FP64 || p->M > se::kFastMaxM)) return SE_ERR_UNSUPPORTED;
     if (spread_variant == 2 && p->prec == SE_FP32) return SE_ERR_UNSUPPORTED;
     p->tune_variant = spread_variant;
     p->tune_tile = tile;
@@ -697,21 +721,21 @@ int se_plan_get_params(const se_plan* p, double* out) {
 int se_spread(se_plan* p, const void* xyz, const void* q) {
     if (!p || (p->N > 0 && (!xyz || !q))) return SE_ERR_ARG;
     SE_TRY(prepare(p));
-    if (p->variant == 3) return fast_spread(p, xyz, q);
+    if (p->variant >= 3) return fast_spread(p, xyz, q);
     return p->prec == SE_FP64 ? do_spread<double>(p, xyz, q) : do_spread<float>(p, xyz, q);
 }
 
 int se_scale(se_plan* p, double* E_grid) {
     if (!p) return SE_ERR_ARG;
     if (!p->ready || !p->have_spread) return SE_ERR_ARG;
-    if (p->variant == 3) return fast_scale(p, E_grid);
+    if (p->variant >= 3) return fast_scale(p, E_grid);
     return p->prec == SE_FP64 ? do_scale<double>(p, E_grid) : do_scale<float>(p, E_grid);
 }
 
 int se_gather(se_plan* p, const void* xyz, const void* q, void* phi, void* F, double* E) {
     if (!p || (p->N > 0 && (!xyz || !q))) return SE_ERR_ARG;
     if (!p->ready || !p->have_scale) return SE_ERR_ARG;
-    if (p->variant == 3) return fast_gather(p, phi, F, E);
+    if (p->variant >= 3) return fast_gather(p, phi, F, E);
     return p->prec == SE_FP64 ? do_gather<double>(p, phi, F, E) : do_gather<float>(p, phi, F, E);
 }
 
@@ -719,7 +743,7 @@ int se_adjoint(se_plan* p, const void* xyz, const void* q, const double* gE, voi
                void* grad_q) {
     if (!p || !gE || (p->N > 0 && (!xyz || !q))) return SE_ERR_ARG;
     if (!p->ready || !p->have_scale) return SE_ERR_ARG;
-    if (p->variant == 3) return fast_gather(p, grad_q, grad_x, nullptr, gE);
+    if (p->variant >= 3) return fast_gather(p, grad_q, grad_x, nullptr, gE);
     return p->prec == SE_FP64 ? do_gather<double>(p, grad_q, grad_x, nullptr, gE)
                               : do_gather<float>(p, grad_q, grad_x, nullptr, gE);
 }
@@ -796,6 +820,12 @@ int se_copy_grid(se_plan* p, int which, void* dst) {
     const size_t bytes = (size_t)p->M * p->M * p->M * tsize(p->prec);
     if (which == 0 && p->variant == 3)
         return check_cuda(se::fast_to_real(fast_bufs(p), p->M, (float*)dst, p->stream));
+    if (which == 0 && p->variant == 4) {
+        // the float grid is cleared by the transform: only between se_spread and se_scale
+        if (p->spread_clean) return SE_ERR_ARG;
+        SE_CUDA(cudaMemcpyAsync(dst, p->g64, bytes, cudaMemcpyDeviceToDevice, p->stream));
+        return SE_OK;
+    }
     SE_CUDA(cudaMemcpyAsync(dst, which == 0 ? p->grid_spread : p->grid_gather, bytes,
                             cudaMemcpyDeviceToDevice, p->stream));
     return SE_OK;

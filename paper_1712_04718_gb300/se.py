@@ -194,6 +194,15 @@ class Plan:
     def set_graph(self, enable=True):
         nat.check(self._lib.se_plan_set_graph(self._h, int(bool(enable))), "se_plan_set_graph")
 
+    def set_tile(self, tile):
+        """Spreading tile edge (grid cells); keeps the automatic pipeline choice."""
+        nat.check(self._lib.se_plan_set_tuning(self._h, 0, int(tile)), "se_plan_set_tuning")
+
+    def set_tuning(self, spread_variant, tile=0):
+        """Spreading variant (0 automatic, 1-4 as in se_plan_set_tuning) and tile edge."""
+        nat.check(self._lib.se_plan_set_tuning(self._h, int(spread_variant), int(tile)),
+                  "se_plan_set_tuning")
+
     def copy_grid(self, which):
         """0: spread grid H (valid after spread), 1: Ht (after scale); [M,M,M] tensor."""
         out = torch.empty((self.M, self.M, self.M), dtype=self.dtype, device="cuda")
@@ -281,6 +290,9 @@ class Batch:
 
     def set_graph(self, enable=True):
         nat.check(self._lib.se_batch_set_graph(self._h, int(bool(enable))), "se_batch_set_graph")
+
+    def set_tile(self, tile):
+        nat.check(self._lib.se_batch_set_tile(self._h, int(tile)), "se_batch_set_tile")
 
     def evaluate(self, xyz, q, F=None, phi=None, E=None):
         """Returns (E [S] float64, F [Ntot,3], phi [Ntot]) CUDA tensors."""

@@ -322,3 +322,123 @@ def test_workload_water_100k_fp32():
     e_gpu, e_o2 = rel(g["F"][idx], F1), rel(r["F"][idx], F1)
     assert e_gpu < e_o2 * 1.01 + 5 * TOL["fp32"]
     assert e_gpu < w["target_rel_force_err"]
+
+
+# ---------------------------------------------------------------------------
+# spread variant 4: the single-precision pipeline with unsorted spreading
+# (global float reductions; the grid's last bits depend on the order of the
+# additions, so the tolerances are those of FP32 rounding, not equality)
+# ---------------------------------------------------------------------------
+
+UNSORTED = [(20, 8), (16, 4), (28, 6), (25, 8), (21, 6), (32, 16), (10, 2), (12, 12), (18, 10)]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32plain"])
+@pytest.mark.parametrize("M,P", UNSORTED)
+def test_unsorted_spread_stage_parity(prec, M, P):
+    L = 2.0
+    xi = min(4.0, math.sqrt(0.8 * 0.95 ** 2 * math.pi * M * M / (P * L * L)))
+    x, q = systems.uniform_charges(301, L, seed=M * 100 + P + 7, dtype=np.float32)
+    q = q.astype(np.float64)
+    q[-1] = -q[:-1].sum()
+    q = q.astype(np.float32)
+    g = run_gpu(x, q, L, xi, M, P, prec, grids=True, spread_variant=4)
+    assert g["params"]["spread_variant"] == 4
+    r = oracle_for(x, q, L, xi, M, P, prec, grids=True)
+    tol = TOL[prec]
+    assert rel(g["H"], r["H"]) < tol, "spread grid"
+    assert rel(g["Ht"], r["Ht"]) < 5 * tol, "scaled grid"
+    assert rel(g["phi"], r["phi"]) < 5 * tol, "phi"
+    assert rel(g["F"], r["F"]) < 5 * tol, "F"
+    assert abs(g["E"] - r["E"]) < 5 * tol * abs(r["E"]), "E"
+    assert abs(g["E_grid"] - r["E_grid"]) < 5 * tol * abs(r["E_grid"]), "E_grid"
+
+
+def test_unsorted_spread_grid_lifecycle():
+    """The float grid is cleared by the transform: repeated evaluations, two
+    spreads in a row (the second replaces the first), graph replays and the
+    adjoint all give the oracle's results; the spread grid is not available
+    after se_scale."""
+    L, xi, M, P = 2.0, 4.0, 24, 6
+    x, q = systems.uniform_charges(400, L, seed=41, dtype=np.float32)
+    x2, q2 = systems.uniform_charges(400, L, seed=42, dtype=np.float32)
+    ref = oracle_for(x, q, L, xi, M, P, "fp32", grids=True)
+    plan = se.Plan(len(q), L, xi, M, P, precision="fp32", spread_variant=4)
+    xd, qd = torch.tensor(x, device="cuda"), torch.tensor(q, device="cuda")
+    xd2, qd2 = torch.tensor(x2, device="cuda"), torch.tensor(q2, device="cuda")
+    for graph in (False, True):
+        plan.set_graph(graph)
+        for _ in range(3):
+            E, F, phi = plan.energy_force(xd, qd)
+            assert rel(F.double().cpu().numpy(), ref["F"]) < 5 * TOL["fp32"]
+            assert abs(E - ref["E"]) < 5 * TOL["fp32"] * abs(ref["E"])
+    plan.spread(xd2, qd2)
+    plan.spread(xd, qd)
+    H = plan.copy_grid(0).double().cpu().numpy()
+    assert rel(H, ref["H"]) < TOL["fp32"]
+    Eg = torch.zeros(1, dtype=torch.float64, device="cuda")
+    plan.scale(Eg)
+    with pytest.raises(nat.SEError) as e:
+        plan.copy_grid(0)
+    assert e.value.status == nat.SE_ERR_ARG
+    gq = torch.empty(len(q), device="cuda")
+    gx = torch.empty((len(q), 3), device="cuda")
+    gE = torch.full((1,), 2.0, dtype=torch.float64, device="cuda")
+    plan.adjoint(xd, qd, gE, gx, gq)
+    torch.cuda.synchronize()
+    assert rel(gx.double().cpu().numpy(), -2.0 * ref["F"]) < 5 * TOL["fp32"]
+    assert rel(gq.double().cpu().numpy(), 2.0 * ref["phi"]) < 5 * TOL["fp32"]
+    plan.close()
+
+
+def test_unsorted_spread_status_checks():
+    L, xi, M, P = 2.0, 4.0, 16, 8
+    x, q = systems.uniform_charges(50, L, seed=43, dtype=np.float32)
+    plan = se.Plan(len(q), L, xi, M, P, precision="fp32", spread_variant=4)
+    xd, qd = torch.tensor(x, device="cuda"), torch.tensor(q, device="cuda")
+    qbad = qd.clone()
+    qbad[0] += 0.5
+    plan.energy_force(xd, qbad)
+    assert plan.last_status == nat.SE_WARN_NONNEUTRAL
+    xbad = xd.clone()
+    xbad[7, 2] = float("inf")
+    with pytest.raises(nat.SEError) as e:
+        plan.energy_force(xbad, qd)
+    assert e.value.status == nat.SE_ERR_NONFINITE
+    E, F, _ = plan.energy_force(xd, qd)     # usable again, grid clean
+    r = oracle_for(x, q, L, xi, M, P, "fp32")
+    assert rel(F.double().cpu().numpy(), r["F"]) < 5 * TOL["fp32"]
+    plan.close()
+
+
+def test_unsorted_spread_water_workload():
+    """The L = 6 water box (21 642 atoms, M = 52, P = 6) through variant 4,
+    elementwise against the oracle."""
+    x, q, w = systems.make("water-L6-M52-P6-fp32comp")
+    g = run_gpu(x, q, w["L"], w["xi"], w["M"], w["P"], "fp32", spread_variant=4)
+    xd, qd = np.asarray(x, np.float64), np.asarray(q, np.float64)
+    r = oracle_for(xd, qd, w["L"], w["xi"], w["M"], w["P"], "fp32")
+    assert rel(g["F"], r["F"]) < 5 * TOL["fp32"]
+    assert rel(g["phi"], r["phi"]) < 5 * TOL["fp32"]
+    assert abs(g["E"] - r["E"]) < 5 * TOL["fp32"] * abs(r["E"])
+
+
+@pytest.mark.parametrize("variant", [3, 4])
+def test_crowded_tile_overflow(variant):
+    """600 of 800 charges inside one spreading tile: the tile's bucket fills
+    and the rest take the overflow path (global fixed-point atomics).  Against
+    the oracle, over repeated evaluations (the overflow count resets itself)
+    and followed by an evaluation without overflow."""
+    L, xi, M, P = 2.0, 4.0, 24, 6
+    rng = np.random.default_rng(51)
+    x, q = systems.uniform_charges(800, L, seed=52, dtype=np.float32)
+    x[:600] = (0.71 + 0.12 * rng.random((600, 3))).astype(np.float32)
+    x2, q2 = systems.uniform_charges(800, L, seed=53, dtype=np.float32)
+    plan = se.Plan(800, L, xi, M, P, precision="fp32", spread_variant=variant, tile=8)
+    for xs, qs in ((x, q), (x, q), (x, q), (x2, q2)):
+        r = oracle_for(xs, qs, L, xi, M, P, "fp32")
+        E, F, phi = plan.energy_force(torch.tensor(xs, device="cuda"), torch.tensor(qs, device="cuda"))
+        assert rel(F.double().cpu().numpy(), r["F"]) < 5 * TOL["fp32"]
+        assert rel(phi.double().cpu().numpy(), r["phi"]) < 5 * TOL["fp32"]
+        assert abs(E - r["E"]) < 5 * TOL["fp32"] * abs(r["E"])
+    plan.close()
