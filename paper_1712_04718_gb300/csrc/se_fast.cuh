@@ -20,9 +20,10 @@
 // one kernel that adds every weight straight into a float grid with global
 // reductions; k_slab_fwd_f reads that grid and clears it for the next call.
 //
-// The 1-D transforms are direct DFTs (M <= 128) written as small complex
-// matrix products with register tiles (se_dft.cuh); twiddles e^{-2 pi i r/M}
-// from a table in shared memory.
+// The 1-D transforms (M <= 128) are small complex matrix products with
+// register tiles (se_dft.cuh): the complex ones factored as M = M1 M2
+// (Cooley-Tukey, two stages), the real-to-complex and complex-to-real ones
+// direct; twiddles e^{-2 pi i r/M} from a table in shared memory.
 #pragma once
 #include <type_traits>
 
@@ -323,13 +324,14 @@ __device__ __forceinline__ void spread_tile(const f4* __restrict__ parts, int n,
         __syncthreads();
         SE_STAMP(2, 3);
         const int ox = t0x - P / 2 + 1 + s0, oy = t0y - P / 2 + 1, oz = t0z - P / 2 + 1;
+        const FDiv fRz = fdiv_of(Rz), fRy = fdiv_of(Ry);
         for (int e = threadIdx.x; e < nel; e += blockDim.x) {
             const unsigned long long v =
                 two ? fx_join2(lo[e], hi[e])
                     : (((unsigned long long)hi[e] << 32) | (unsigned long long)lo[e]);
             if (v != 0ull) {
-                const int rz = e % Rz, r = e / Rz;
-                const int ry = r % Ry, rx = r / Ry;
+                const int r = fdiv(e, fRz), rz = e - r * Rz;
+                const int rx = fdiv(r, fRy), ry = r - rx * Ry;
                 const int gx_ = wrap_index(ox + rx, M), gy_ = wrap_index(oy + ry, M),
                           gz_ = wrap_index(oz + rz, M);
                 atomicAdd(g64 + ((size_t)gx_ * M + gy_) * M + gz_, v);
@@ -620,15 +622,21 @@ __device__ __forceinline__ void load_twiddles(float2* tw, const float2* __restri
 }
 
 // shared memory of the slab kernels: tw[M] | A: M x (M+1) floats, or the
-// M x Mh complex slab | T: Mh x (M+1) complex
+// M x Mh complex slab | T: Mh x (M+1) complex | Z: M x Mh complex (scratch
+// of the factored DFTs)
 __host__ __device__ inline size_t slab_a_bytes(int M) {
     const size_t Mh = M / 2 + 1, SP = M + 1;
     const size_t a = (size_t)M * SP * sizeof(float), c = (size_t)M * Mh * sizeof(float2);
     return ((a > c ? a : c) + 15) / 16 * 16;
 }
-__host__ __device__ inline size_t slab_smem_bytes(int M) {
+__host__ __device__ inline size_t slab_t_bytes(int M) {
     const size_t Mh = M / 2 + 1, SP = M + 1;
-    return (size_t)M * sizeof(float2) + slab_a_bytes(M) + Mh * SP * sizeof(float2);
+    return Mh * SP * sizeof(float2);
+}
+__host__ __device__ inline size_t slab_smem_bytes(int M) {
+    const size_t Mh = M / 2 + 1;
+    return (size_t)M * sizeof(float2) + slab_a_bytes(M) + slab_t_bytes(M) +
+           (size_t)M * Mh * sizeof(float2);
 }
 
 // Forward 2-D transform (z real-to-complex, then y) of x-slab x.  The input
@@ -642,8 +650,11 @@ __device__ __forceinline__ void slab_fwd_body(G* __restrict__ grid, float2* __re
     float2* tw = reinterpret_cast<float2*>(sm);
     float* S = reinterpret_cast<float*>(sm + (size_t)M * sizeof(float2));
     float2* T = reinterpret_cast<float2*>(sm + (size_t)M * sizeof(float2) + slab_a_bytes(M));
+    float2* Z = reinterpret_cast<float2*>(sm + (size_t)M * sizeof(float2) + slab_a_bytes(M) +
+                                          slab_t_bytes(M));
     load_twiddles(tw, tw_g, M);
     G* src = grid + (size_t)x * M * M;
+    const FDiv fM = fdiv_of(M);
     // kLoadBatch loads per thread in flight before any is used
     for (int e0 = threadIdx.x; e0 < M * M; e0 += blockDim.x * kLoadBatch) {
         std::remove_const_t<G> v[kLoadBatch];
@@ -656,7 +667,7 @@ __device__ __forceinline__ void slab_fwd_body(G* __restrict__ grid, float2* __re
         for (int u = 0; u < kLoadBatch; ++u) {
             const int e = e0 + u * (int)blockDim.x;
             if (e >= M * M) break;
-            const int y = e / M, z = e - y * M;
+            const int y = fdiv(e, fM), z = e - y * M;
             if constexpr (sizeof(G) == sizeof(float)) {
                 S[y * SP + z] = v[u];
                 src[e] = 0.0f;
@@ -675,7 +686,7 @@ __device__ __forceinline__ void slab_fwd_body(G* __restrict__ grid, float2* __re
     __syncthreads();
     SE_STAMP(3, 3);
     // y forward: X(j = y, c = kz) = T[kz][y]  ->  C[x][ky][kz]
-    dft_c2c<2, 2>(T, 1, SP, C + (size_t)x * M * Mh, Mh, 1, M, M, Mh, tw, M, -1.0f);
+    dft_c2c_fact(T, 1, SP, C + (size_t)x * M * Mh, Mh, 1, Mh, Z, tw, M, -1.0f);
     SE_STAMP(3, 4);
 }
 
@@ -712,11 +723,13 @@ __device__ __forceinline__ df2 xpass_body(float2* __restrict__ C, const float2* 
     __shared__ float2 tw[kFastMaxM];
     __shared__ float2 s[kFastMaxM * kFastKC];
     __shared__ float2 s2[kFastMaxM * kFastKC];
+    __shared__ float2 s3[kFastMaxM * kFastKC];   // scratch of the factored DFTs
     __shared__ df2 sbuf[32];
     const int Mh = M / 2 + 1;
     const int nch = (Mh + kFastKC - 1) / kFastKC;
     const int y = item / nch, c0 = (item % nch) * kFastKC;
     const int nc = min(kFastKC, Mh - c0);
+    const FDiv fnc = fdiv_of(nc);
     load_twiddles(tw, tw_g, M);
     for (int e0 = threadIdx.x; e0 < M * nc; e0 += blockDim.x * kLoadBatch) {
         float2 v[kLoadBatch];
@@ -724,7 +737,7 @@ __device__ __forceinline__ df2 xpass_body(float2* __restrict__ C, const float2* 
         for (int u = 0; u < kLoadBatch; ++u) {
             const int e = e0 + u * (int)blockDim.x;
             if (e < M * nc) {
-                const int x = e / nc, kk = e - x * nc;
+                const int x = fdiv(e, fnc), kk = e - x * nc;
                 v[u] = C[((size_t)x * M + y) * Mh + c0 + kk];
             }
         }
@@ -732,19 +745,19 @@ __device__ __forceinline__ df2 xpass_body(float2* __restrict__ C, const float2* 
         for (int u = 0; u < kLoadBatch; ++u) {
             const int e = e0 + u * (int)blockDim.x;
             if (e < M * nc) {
-                const int x = e / nc, kk = e - x * nc;
+                const int x = fdiv(e, fnc), kk = e - x * nc;
                 s[x * kFastKC + kk] = v[u];
             }
         }
     }
     __syncthreads();
     SE_STAMP(4, 2);
-    dft_c2c<2, 2>(s, kFastKC, 1, s2, kFastKC, 1, M, M, nc, tw, M, -1.0f);
+    dft_c2c_fact(s, kFastKC, 1, s2, kFastKC, 1, nc, s3, tw, M, -1.0f);
     __syncthreads();
     SE_STAMP(4, 3);
     df2 en = df_from(0.0f);   // double-float energy sum
     for (int e = threadIdx.x; e < M * nc; e += blockDim.x) {
-        const int kx = e / nc, kk = e - kx * nc;
+        const int kx = fdiv(e, fnc), kk = e - kx * nc;
         const int kz = c0 + kk;
         const float2 v = s2[kx * kFastKC + kk];
         const float g = green[((size_t)kx * M + y) * Mh + kz];
@@ -754,7 +767,7 @@ __device__ __forceinline__ df2 xpass_body(float2* __restrict__ C, const float2* 
         s2[kx * kFastKC + kk] = make_float2(v.x * f, v.y * f);
     }
     __syncthreads();
-    dft_c2c<2, 2>(s2, kFastKC, 1, C + (size_t)y * Mh + c0, (size_t)M * Mh, 1, M, M, nc, tw, M, 1.0f);
+    dft_c2c_fact(s2, kFastKC, 1, C + (size_t)y * Mh + c0, M * Mh, 1, nc, s3, tw, M, 1.0f);
     SE_STAMP(4, 4);
     return block_sum_df(en, sbuf);
 }
@@ -797,6 +810,8 @@ __device__ __forceinline__ void slab_inv_body(const float2* __restrict__ C, floa
     float* S = reinterpret_cast<float*>(sm + (size_t)M * sizeof(float2));
     float2* A = reinterpret_cast<float2*>(S);   // the slab, before S is needed
     float2* T = reinterpret_cast<float2*>(sm + (size_t)M * sizeof(float2) + slab_a_bytes(M));
+    float2* Z = reinterpret_cast<float2*>(sm + (size_t)M * sizeof(float2) + slab_a_bytes(M) +
+                                          slab_t_bytes(M));
     load_twiddles(tw, tw_g, M);
     const float2* src = C + (size_t)x * M * Mh;
     for (int e0 = threadIdx.x; e0 < M * Mh; e0 += blockDim.x * kLoadBatch) {
@@ -815,11 +830,12 @@ __device__ __forceinline__ void slab_inv_body(const float2* __restrict__ C, floa
     __syncthreads();
     // y inverse: X(j = ky, c = kz) = A[ky][kz]  ->  T[kz][y], with the
     // Hermitian weights of the z real transform (1 at kz = 0 and M/2, else 2)
-    dft_c2c<2, 2>(A, Mh, 1, T, 1, SP, M, M, Mh, tw, M, 1.0f);
+    dft_c2c_fact(A, Mh, 1, T, 1, SP, Mh, Z, tw, M, 1.0f);
     __syncthreads();
     SE_STAMP(5, 2);
+    const FDiv fM = fdiv_of(M);
     for (int e = threadIdx.x; e < Mh * M; e += blockDim.x) {
-        const int kz = e / M, y = e - kz * M;
+        const int kz = fdiv(e, fM), y = e - kz * M;
         if (kz != 0 && 2 * kz != M) {
             float2 v = T[kz * SP + y];
             T[kz * SP + y] = make_float2(2.f * v.x, 2.f * v.y);
@@ -832,7 +848,7 @@ __device__ __forceinline__ void slab_inv_body(const float2* __restrict__ C, floa
     SE_STAMP(5, 3);
     float* dst = R + (size_t)x * M * M;
     for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
-        const int y = e / M, z = e - y * M;
+        const int y = fdiv(e, fM), z = e - y * M;
         dst[e] = S[y * SP + z];
     }
     SE_STAMP(5, 4);

@@ -130,10 +130,26 @@ __host__ __device__ constexpr int pick_d(int P) {
 
 constexpr int kScanSmem = 8192;   // tile counts staged in shared memory by the scan
 
+// Periodic grid index for i in [-M, 2M): every caller passes a support index
+// c - P/2 + 1 + a (0 <= c < M, 0 <= a < P) or a tile region offset of the
+// same range, and every entry point enforces P <= M.
 __device__ __forceinline__ int wrap_index(int i, int M) {
-    i %= M;
-    return i < 0 ? i + M : i;
+    if (i < 0) i += M;
+    if (i >= M) i -= M;
+    return i;
 }
+
+// Quotient n / d of integers 0 <= n < 2^22, d > 0, from a float reciprocal:
+// (n + 1/2) / d lies at least 1/(2d) from an integer, and the two roundings
+// (reciprocal and product) move it by less than (n + 1/2) 2^-23 / d < 1/(2d),
+// so truncation gives the exact quotient.  A few instructions instead of the
+// long integer division sequence, in index arithmetic of the hot loops.
+struct FDiv {
+    float inv;
+    int d;
+};
+__device__ __forceinline__ FDiv fdiv_of(int d) { return FDiv{__frcp_rn((float)d), d}; }
+__device__ __forceinline__ int fdiv(int n, FDiv f) { return (int)(((float)n + 0.5f) * f.inv); }
 
 // Block-wide sum of one double (blockDim.x a multiple of 32, <= 1024).
 __device__ __forceinline__ double block_sum(double v, double* sbuf) {
@@ -441,12 +457,13 @@ k_spread_tiled(const v4_t<T>* __restrict__ sorted, const int* __restrict__ tile_
         }
         __syncthreads();
         const int ox = t0x - P / 2 + 1 + s0, oy = t0y - P / 2 + 1, oz = t0z - P / 2 + 1;
+        const FDiv fRz = fdiv_of(Rz), fRy = fdiv_of(Ry);
         for (int e = threadIdx.x; e < nel; e += blockDim.x) {
             T val = hi[e];
             if (COMP) val = add_rn(val, lo[e]);
             if (val != T(0)) {
-                const int rz = e % Rz, r = e / Rz;
-                const int ry = r % Ry, rx = r / Ry;
+                const int r = fdiv(e, fRz), rz = e - r * Rz;
+                const int rx = fdiv(r, fRy), ry = r - rx * Ry;
                 const int gx_ = wrap_index(ox + rx, M), gy_ = wrap_index(oy + ry, M),
                           gz_ = wrap_index(oz + rz, M);
                 atomicAdd(grid + ((size_t)gx_ * M + gy_) * M + gz_, val);

@@ -330,7 +330,10 @@ def test_workload_water_100k_fp32():
 # additions, so the tolerances are those of FP32 rounding, not equality)
 # ---------------------------------------------------------------------------
 
-UNSORTED = [(20, 8), (16, 4), (28, 6), (25, 8), (21, 6), (32, 16), (10, 2), (12, 12), (18, 10)]
+# the grid sizes cover the DFT factorisations M = M1 M2 with M1 = 2, 3, 4, 5
+# and the direct transform of a prime M (23, 29)
+UNSORTED = [(20, 8), (16, 4), (28, 6), (25, 8), (21, 6), (32, 16), (10, 2), (12, 12), (18, 10),
+            (23, 6), (29, 8)]
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp32plain"])
