@@ -537,7 +537,7 @@ int prepare_batch(se_batch* b) {
 template <int P>
 cudaError_t launch_bspread(se_batch* b, cudaStream_t s) {
     const size_t R = (size_t)b->tile + P - 1;
-    const size_t plane = R * R * 2 * sizeof(unsigned);
+    const size_t plane = R * R * sizeof(unsigned);   // one 32-bit accumulator per point
     const int slab = (int)std::min(R, se::kSmemBudget / plane);
     if (slab < 1) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(se::k_bspread<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,

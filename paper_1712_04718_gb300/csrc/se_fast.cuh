@@ -4,11 +4,12 @@
 //   k_fbin      tile of each particle and a slot in the tile's bucket (a
 //               fixed-capacity list; full buckets spill to an overflow list),
 //               q sums and max |q|; clears the fixed-point spread grid
-//   k_fspread   Eq. 3.5, one CTA per tile, exact 64-bit fixed-point sums in
-//               shared memory (two native 32-bit atomics per weight), flushed
-//               with global 64-bit integer reductions: the grid is the same
-//               for any order of the additions; a few more CTAs add the
-//               overflow list with global 64-bit atomics
+//   k_fspread   Eq. 3.5, one CTA per tile: 32-bit fixed-point sums in shared
+//               memory at a per-tile scale (one native 32-bit atomic per
+//               weight), flushed exactly into the 64-bit fixed-point grid with
+//               global integer reductions: the grid is the same for any order
+//               of the additions; a few more CTAs add the overflow list with
+//               global 64-bit atomics
 //   k_slab_fwd  per x-slab: forward DFT along z (real to complex; the
 //               fixed-point grid is converted to float here), then along y
 //   k_xpass     forward DFT along x, scaling by G(k)/M^3 (Eq. 3.6) with the
@@ -206,49 +207,22 @@ __device__ __forceinline__ void fx_split(float v, unsigned* vh, unsigned* vl) {
     }
 }
 
-// One weight into a 64-bit fixed-point accumulator held as (hi, lo) 32-bit
-// words in shared memory: lo gets the low word and reports its carry, hi the
-// high word plus the carry.  Two's-complement addition modulo 2^64, exact and
-// independent of the order of the additions.
-__device__ __forceinline__ void fx_add(unsigned* hi, unsigned* lo, float v) {
-    unsigned vl, vh;
-    fx_split(v, &vh, &vl);
-    const unsigned old = atomicAdd(lo, vl);
-    const unsigned carry = (old + vl < old) ? 1u : 0u;
-    atomicAdd(hi, vh + carry);
-}
-
-// A scaled weight v (|v| < 2^40) rounded to an integer V and added as two
-// pieces to two 32-bit words with non-returning atomics: V mod 2^21 to the
-// first (unsigned) and floor(V / 2^21) to the second (signed).  No carry, so
-// no atomic waits on another.  The first word cannot overflow while a point
-// receives fewer than 2^11 weights, i.e. while a tile holds fewer than 2048
-// particles; the second (|piece| < 2^19) neither.  The split is exact in
-// FP32: V = rint(v) is exact for |v| < 2^24 and v is already an integer
-// beyond; floor(V 2^-21) is exact; V - 2^21 floor(V 2^-21) lies in [0, 2^21)
-// on V's ulp grid and is representable.
-__device__ __forceinline__ void fx_add2(unsigned* w0, unsigned* w1, float v) {
-    const float vr = rintf(v);
-    const float hf = floorf(vr * 4.76837158203125e-7f);   // 2^-21
-    const float lf = fmaf(-hf, 2097152.0f, vr);           // exact, in [0, 2^21)
-    atomicAdd(w0, __float2uint_rn(lf));
-    atomicAdd(w1, (unsigned)__float2int_rn(hf));
-}
-
-__device__ __forceinline__ unsigned long long fx_join2(unsigned a0, unsigned a1) {
-    return ((unsigned long long)(long long)(int)a1 << 21) + (unsigned long long)a0;
-}
-
-// Spread of one tile (Eq. 3.5) into the fixed-point grid g64: the n
-// particles parts[0..n) of the tile; fxs is the fixed-point scale.  Called by
-// one whole block (uniformly: the early return is per block).
+// Spread of one tile (Eq. 3.5) into the fixed-point grid g64 (scale fxs =
+// 2^k): the n particles parts[0..n) of the tile.  The tile's region is
+// accumulated in shared memory as one 32-bit integer per point at the scale
+// 2^kt, kt = k - s, s = 10 + ceil(log2 n): every weight is at most
+// B = c_g max|q| = 2^(40-k), so a point's sum is at most n B 2^kt <= 2^30 and
+// cannot overflow; each weight is rounded once to an integer there (a
+// quantum of n 2^-30 B at most) and added with one native 32-bit atomic, and
+// the region is flushed exactly into the 64-bit grid by a shift of s bits.
+// Integer additions: the grid does not depend on their order.  Called by one
+// whole block (uniformly: the early return is per block).
 template <int P>
 __device__ __forceinline__ void spread_tile(const f4* __restrict__ parts, int n,
                                             unsigned long long* __restrict__ g64,
                                             const KParams<float>& kp, float fxs, int slab,
-                                            int tile, unsigned* hi, float* sE3) {
+                                            int tile, unsigned* acc, float* sE3) {
     constexpr int D = pick_d(P), G = P / D, GPW = 32 / G;
-    const int pbeg = 0, pend = n;
     if (n <= 0) return;
     if (threadIdx.x < P) sE3[threadIdx.x] = kp.E3[threadIdx.x];
     const int nT = kp.nT, M = kp.M, TT = kp.tile;
@@ -257,9 +231,8 @@ __device__ __forceinline__ void spread_tile(const f4* __restrict__ parts, int n,
     const int Ry = min(TT, M - t0y) + P - 1, Rz = min(TT, M - t0z) + P - 1;
     const int Rx = min(TT, M - t0x) + P - 1;
     const int plane = Ry * Rz;
-    unsigned* lo = hi + (size_t)slab * plane;
-    // fewer than 2048 particles: two carry-free pieces; else (hi, lo) with carries
-    const bool two = (pend - pbeg) < 2048;
+    const int shift = 10 + (n > 1 ? 32 - __clz(n - 1) : 0);   // 10 + ceil(log2 n)
+    const float fxt = ldexpf(fxs, -shift);
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gi = lane / G, k = lane - gi * G;
@@ -270,14 +243,11 @@ __device__ __forceinline__ void spread_tile(const f4* __restrict__ parts, int n,
     for (int s0 = 0; s0 < Rx; s0 += slab) {
         const int ns = min(slab, Rx - s0);
         const int nel = ns * plane;
-        for (int e = threadIdx.x; e < nel; e += blockDim.x) {
-            hi[e] = 0u;
-            lo[e] = 0u;
-        }
+        for (int e = threadIdx.x; e < nel; e += blockDim.x) acc[e] = 0u;
         __syncthreads();
         SE_STAMP(2, 2);
         if (act) {
-            for (int p = pbeg + group; p < pend; p += ngroups) {
+            for (int p = group; p < n; p += ngroups) {
                 const f4 v = parts[p];
                 float t;
                 const int cx = cell_of(v.x, kp.invh, M, &t);
@@ -292,7 +262,7 @@ __device__ __forceinline__ void spread_tile(const f4* __restrict__ parts, int n,
                 float gy[P];
                 fgg<float, P>(uy, kp.beta, kp.E3, gy);
                 float gz[D];
-                const float qw = v.w * kp.qcg * fxs;
+                const float qw = v.w * kp.qcg * fxt;
 #pragma unroll
                 for (int j = 0; j < D; ++j) {
                     const float dz = float(k + j * G) - 0.5f * float(P - 1) - uz;
@@ -300,24 +270,19 @@ __device__ __forceinline__ void spread_tile(const f4* __restrict__ parts, int n,
                 }
                 const float Bx = expf(2.0f * kp.beta * ux);
                 float px = expf(-kp.beta * ux * (ux + float(P - 1)) + 2.0f * kp.beta * ux * float(alo));
+                unsigned* row = acc + ((lx + alo - s0) * Ry + ly) * Rz + lz + k;
 #pragma unroll 1
                 for (int a = alo; a < ahi; ++a) {
                     const float gxa = px * sE3[a];
                     px *= Bx;
-                    const int rowx = lx + a - s0;
-                    const int rowoff = (rowx * Ry + ly) * Rz + lz + k;
 #pragma unroll
                     for (int b = 0; b < P; ++b) {
                         const float wab = gxa * gy[b];
 #pragma unroll
-                        for (int j = 0; j < D; ++j) {
-                            const int e = rowoff + b * Rz + j * G;
-                            if (two)
-                                fx_add2(lo + e, hi + e, wab * gz[j]);
-                            else
-                                fx_add(hi + e, lo + e, wab * gz[j]);
-                        }
+                        for (int j = 0; j < D; ++j)
+                            atomicAdd(row + b * Rz + j * G, (unsigned)__float2int_rn(wab * gz[j]));
                     }
+                    row += plane;
                 }
             }
         }
@@ -326,15 +291,14 @@ __device__ __forceinline__ void spread_tile(const f4* __restrict__ parts, int n,
         const int ox = t0x - P / 2 + 1 + s0, oy = t0y - P / 2 + 1, oz = t0z - P / 2 + 1;
         const FDiv fRz = fdiv_of(Rz), fRy = fdiv_of(Ry);
         for (int e = threadIdx.x; e < nel; e += blockDim.x) {
-            const unsigned long long v =
-                two ? fx_join2(lo[e], hi[e])
-                    : (((unsigned long long)hi[e] << 32) | (unsigned long long)lo[e]);
-            if (v != 0ull) {
+            const int w = (int)acc[e];
+            if (w != 0) {
                 const int r = fdiv(e, fRz), rz = e - r * Rz;
                 const int rx = fdiv(r, fRy), ry = r - rx * Ry;
                 const int gx_ = wrap_index(ox + rx, M), gy_ = wrap_index(oy + ry, M),
                           gz_ = wrap_index(oz + rz, M);
-                atomicAdd(g64 + ((size_t)gx_ * M + gy_) * M + gz_, v);
+                atomicAdd(g64 + ((size_t)gx_ * M + gy_) * M + gz_,
+                          (unsigned long long)((long long)w << shift));
             }
         }
         __syncthreads();

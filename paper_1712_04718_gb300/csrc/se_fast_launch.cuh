@@ -19,7 +19,7 @@ inline int fast_bin_blocks(const KParams<float>& kp) {
 template <int P>
 cudaError_t fast_spread_P(const KParams<float>& kp, const FastBufs& b, int nbin, cudaStream_t s) {
     const size_t R = (size_t)kp.tile + P - 1;
-    const size_t plane = R * R * 2 * sizeof(unsigned);
+    const size_t plane = R * R * sizeof(unsigned);   // one 32-bit accumulator per point
     const int slab = (int)std::min(R, kSmemBudget / plane);
     if (slab < 1) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_fspread<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
