@@ -34,8 +34,6 @@ if ROOT not in sys.path:
 
 DEFAULT_WORKLOAD = "water-L6-M52-P6-fp32comp"
 METRIC = "SE k-space energy+force evals/s and ns/atom at stated rms force error vs FP64"
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
-FP64_PEAK_TFLOPS = 1.25                              # nominal GB300 FP64
 
 
 def parse_args():
@@ -118,32 +116,111 @@ def workload(name):
     return x, q, w, prec
 
 
-def stage_work(w, prec, N, fast):
-    """Algorithmic work of each own kernel per launch: (kind, amount).
-    spread: N P^3 weights, each a multiply and an add (2 flops);
+def dft_split(M):
+    """M1 of the factored transforms: the largest divisor of M not above sqrt(M)."""
+    best, a = 1, 2
+    while a * a <= M:
+        if M % a == 0:
+            best = a
+        a += 1
+    return best
+
+
+def stage_work(w, prec, N, variant):
+    """Algorithmic work of each own kernel per launch: (kind, amount, kernel).
+
+    spread (variants 3, 4): N P^3 weights; in the sorted pipeline each is one
+      native 32-bit shared-memory atomic add ("smem_atomic"), otherwise a
+      multiply and an add (2 flops);
     gather: N P^3 grid values, each two FMAs (4 flops);
-    single-precision pipeline (fast): the slab kernels do the z and y direct
-    DFTs (M^3 (M/2+1) complex multiply-adds each: 8 flops complex, 4 for the
-    real-to-complex / complex-to-real one), the x pass two complex ones;
+    single-precision pipeline: the z transforms are direct real DFTs (M^2 rows
+      x M inputs x (M/2+1) outputs, 2 FMAs = 4 flops each); the y and x
+      transforms are factored complex DFTs, M (M1 + M/M1) complex multiply-adds
+      (8 flops) per column of length M; the x pass does two of them and the
+      scaling (about 6 flops per mode);
     cuFFT pipeline: scale reads and writes the half spectrum and the G table
-    (bytes); bin/scatter: particle bytes."""
+      (bytes); bin/scatter: particle bytes."""
     P, M = w["P"], w["M"]
     Mh = M // 2 + 1
     ts = 8 if prec == "fp64" else 4
     nc = M * M * Mh
+    fast = variant in (3, 4)
+    M1 = dft_split(M)
+    cplx = 8.0 * M * (M1 + M // M1) * (M * Mh) if M1 > 1 else 8.0 * M * M * (M * Mh)
+    real = 4.0 * M ** 3 * Mh
     work = {
-        "spread": ("flop", 2.0 * N * P ** 3),
-        "gather": ("flop", 4.0 * N * P ** 3),
-        "bin": ("byte", N * (4 * ts + 8)),
-        "scatter": ("byte", N * (4 * ts + 4 * ts + 8 + 4)),
+        "spread": (("smem_atomic", float(N) * P ** 3, "k_fspread") if variant == 3 else
+                   ("flop", 2.0 * N * P ** 3, "k_fdirect" if variant == 4 else "k_spread")),
+        "gather": ("flop", 4.0 * N * P ** 3, "k_gather"),
+        "bin": ("byte", N * (4 * ts + 8), "k_fbin" if variant == 3 else "k_bin"),
+        "scatter": ("byte", N * (4 * ts + 4 * ts + 8 + 4), "k_scatter"),
     }
     if fast:
-        work["fft_fwd"] = ("flop", 12.0 * M ** 3 * Mh)
-        work["scale"] = ("flop", 16.0 * M ** 3 * Mh)
-        work["fft_inv"] = ("flop", 12.0 * M ** 3 * Mh)
+        work["fft_fwd"] = ("flop", real + cplx, "k_slab_fwd")
+        work["scale"] = ("flop", 2 * cplx + 6.0 * nc, "k_xpass")
+        work["fft_inv"] = ("flop", cplx + real, "k_slab_inv")
     else:
-        work["scale"] = ("byte", nc * (4 * ts + 8) + M ** 3 * ts)
+        work["scale"] = ("byte", nc * (4 * ts + 8) + M ** 3 * ts, "k_scale")
     return work
+
+
+def kernel_sources_sha():
+    """Digest of the single-precision kernel sources (an ncu summary applies
+    only to the sources it was taken on)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("se_fast.cuh", "se_fast_launch.cuh", "se_kernels.cuh", "se_dft.cuh",
+              "se_internal.h"):
+        with open(os.path.join(ROOT, "paper_1712_04718_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, workload_name):
+    """DRAM bytes per launch (read + write) of `kernel` on `workload_name` from
+    the committed ncu summary profiles/ncu_<kernel>_<workload>.md, or None
+    when there is none or it was taken on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_%s_%s.md" % (kernel, workload_name))
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        line = line.strip().lstrip("-* ").strip()
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip().strip("`")] = v.strip().strip("`")
+    if vals.get("kernel_sources_sha256") != kernel_sources_sha():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def roofline(kind, amount, kernel, secs, prec, peaks, workload_name):
+    """Roofline object of one kernel: achieved rate of its bounding unit over
+    that unit's measured peak."""
+    from paper_1712_04718_gb300 import se
+    if kind == "smem_atomic":
+        pk = se.probe_peak("smem_atomic_u32") / 1e9
+        achieved = amount / secs / 1e9
+        r = {"bound": "alu", "unit": "Gop/s", "peak_source":
+             "measured: se_probe_peak shared-memory u32 atomic adds (this run)",
+             "fp32_tflops": 2.0 * amount / secs / 1e12}
+    elif kind == "flop":
+        pk = se.probe_peak("fp64_fma" if prec == "fp64" else "fp32_fma") / 1e12
+        achieved = amount / secs / 1e12
+        r = {"bound": "alu", "unit": "TFLOP/s", "peak_source":
+             "measured: se_probe_peak %s FMA (this run)" % ("FP64" if prec == "fp64" else "FP32")}
+    else:
+        pk = peaks.get("hbm_gbs", 6800.0)
+        achieved = amount / secs / 1e9
+        r = {"bound": "hbm", "unit": "GB/s",
+             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"}
+    r.update({"kernel": kernel, "achieved": achieved, "peak": pk, "frac": achieved / pk,
+              "traffic": profiled_traffic(kernel, workload_name),
+              "work_per_launch": amount, "launch_us": secs * 1e6})
+    return r
 
 
 def run_ours(args):
@@ -235,31 +312,23 @@ def run_ours(args):
 
     # roofline of the dominant own kernel (average launch duration from events)
     fast = variant in (3, 4)
-    work = stage_work(w, prec, N, fast)
+    work = stage_work(w, prec, N, variant)
     per_launch_ms = {k: v / max(1, nstage) for k, v in stages.items()}
-    own = ["bin", "scatter", "spread", "scale", "gather"]
+    own = [k for k in ("bin", "scatter", "spread", "scale", "gather") if k in work]
     if fast:
         own += ["fft_fwd", "fft_inv"]   # the transforms are own kernels there
+    if variant in (3, 4):
+        own.remove("scatter")           # no scatter kernel in these pipelines
+    if variant == 4:
+        own.remove("bin")
     dom = max(own, key=lambda k: per_launch_ms[k])
-    kind, amount = work[dom]
-    secs = per_launch_ms[dom] / 1e3
+    kind, amount, kname = work[dom]
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    if kind == "flop":
-        pk = FP64_PEAK_TFLOPS if prec == "fp64" else FP32_PEAK_TFLOPS
-        achieved = amount / secs / 1e12
-        roof = {"bound": "alu", "kernel": "k_" + dom, "achieved": achieved, "peak": pk,
-                "unit": "TFLOP/s", "frac": achieved / pk, "traffic": None,
-                "peak_source": ("nominal FP64" if prec == "fp64" else
-                                "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"),
-                "work_per_launch": amount}
-    else:
-        pk = peaks.get("hbm_gbs", 6800.0)
-        achieved = amount / secs / 1e9
-        roof = {"bound": "hbm", "kernel": "k_" + dom, "achieved": achieved, "peak": pk,
-                "unit": "GB/s", "frac": achieved / pk, "traffic": None,
-                "peak_source": "measured" if peaks else "fallback", "work_per_launch": amount}
-    roof["launch_us"] = per_launch_ms[dom] * 1e3
+    roof = roofline(kind, amount, kname, per_launch_ms[dom] / 1e3, prec, peaks, args.workload)
+    roof["all_kernels"] = {
+        work[k][2]: {"us": per_launch_ms[k] * 1e3, "work": work[k][1], "kind": work[k][0]}
+        for k in own}
 
     out = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": K,
@@ -279,9 +348,9 @@ def run_ours(args):
                        "replays one CUDA graph per evaluation)" % nstage,
         "fft_us_per_eval": (stages["fft_fwd"] + stages["fft_inv"]) / max(1, nstage) * 1e3,
         "roofline": roof,
-        "gpu_launches": {3: 7, 4: 5}.get(variant, 5) * K,
+        "gpu_launches": {3: 6, 4: 5}.get(variant, 5) * K,
         "gpu_launches_note": {
-            3: "own kernels per step: bin, scatter, spread, slab_fwd, xpass, slab_inv, gather",
+            3: "own kernels per step: bin, spread, slab_fwd, xpass, slab_inv, gather",
             4: "own kernels per step: spread (unsorted), slab_fwd, xpass, slab_inv, gather"}.get(
                 variant, "own kernels per step: bin, scatter, spread, scale, gather (+ cuFFT)"),
         "clocks": clk,
@@ -293,6 +362,8 @@ def run_ours(args):
         if args.workload == DEFAULT_WORKLOAD:
             out["at_target"] = at_target(se, torch, x, q, w, prec, K, flush)
         out["no_graph"] = no_graph(se, torch, plan, xd, qd, F, phi, Ed, flush, min(K, 1000))
+        if prec != "fp64" and w["M"] <= 128:
+            out["unsorted_variant"] = unsorted_variant(se, torch, x, q, w, prec, min(K, 1000), flush)
         out["cpu_baseline"] = cpu_baseline(x, q, w, args.cpu_seconds)
     plan.close()
     if ws > 1:
@@ -465,6 +536,32 @@ def at_target(se, torch, x, q, w, prec, K, flush):
                 "value": 1e3 / ms, "unit": "evals/s", "ms_per_step": ms,
                 "ns_per_atom": ms * 1e6 / N, "rel_rms_force_err": err, "steps": k}
     return None
+
+
+def unsorted_variant(se, torch, x, q, w, prec, K, flush):
+    """The same evaluation with spread variant 4 (no sort: global float
+    reductions straight into the grid) instead of the shared-memory tiles."""
+    N = len(q)
+    plan = se.Plan(N, w["L"], w["xi"], w["M"], w["P"], precision=prec, spread_variant=4)
+    dt = plan.dtype
+    xd = torch.tensor(x, dtype=dt, device="cuda")
+    qd = torch.tensor(q, dtype=dt, device="cuda")
+    F = torch.empty((N, 3), dtype=dt, device="cuda")
+    phi = torch.empty((N,), dtype=dt, device="cuda")
+    for _ in range(10):
+        plan.evaluate(xd, qd, F, phi)
+    st = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    en = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    for i in range(K):
+        flush()
+        st[i].record()
+        plan.evaluate(xd, qd, F, phi)
+        en[i].record()
+    torch.cuda.synchronize()
+    plan.close()
+    ms = sum(a.elapsed_time(b) for a, b in zip(st, en)) / K
+    return {"spread_variant": 4, "value": 1e3 / ms, "unit": "evals/s", "ms_per_step": ms,
+            "steps": K}
 
 
 def no_graph(se, torch, plan, xd, qd, F, phi, Ed, flush, K):

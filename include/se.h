@@ -256,6 +256,20 @@ int se_plan_set_timing(se_plan *plan, int enable);
  * *count; reset = 1 clears the sums afterwards. */
 int se_plan_get_timing(se_plan *plan, double *ms, int nstages, int64_t *count, int reset);
 
+/* Throughput probe of the current GPU (measurement helper; the paper has no
+ * counterpart): runs a short timed kernel on a private stream, waits for it,
+ * and writes to *out the rate of one unit that bounds the spread, gather and
+ * transform kernels: SE_PROBE_FP32_FMA and SE_PROBE_FP64_FMA in flop/s (an
+ * FMA counts 2), SE_PROBE_SMEM_ATOMIC_U32 and SE_PROBE_SMEM_ATOMIC_F32 in
+ * shared-memory atomic adds per second (non-returning, no bank conflicts).
+ * About a millisecond of GPU time; allocates a small device buffer.
+ * SE_ERR_ARG for an unknown kind or a null out. */
+#define SE_PROBE_FP32_FMA 0
+#define SE_PROBE_FP64_FMA 1
+#define SE_PROBE_SMEM_ATOMIC_U32 2
+#define SE_PROBE_SMEM_ATOMIC_F32 3
+int se_probe_peak(int kind, double *out);
+
 /* Library version as major*10000 + minor*100 + patch. */
 int se_version(void);
 

@@ -22,6 +22,10 @@ SE_ERR_NONFINITE = -6
 SE_FP64 = 0
 SE_FP32 = 1
 SE_FP32_PLAIN = 2
+SE_PROBE_FP32_FMA = 0
+SE_PROBE_FP64_FMA = 1
+SE_PROBE_SMEM_ATOMIC_U32 = 2
+SE_PROBE_SMEM_ATOMIC_F32 = 3
 
 # name -> (restype, argtypes)
 _vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
@@ -61,6 +65,7 @@ SIGNATURES = {
     "se_batch_autotune": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i, _i, ctypes.POINTER(_i),
                                ctypes.POINTER(ctypes.c_float)]),
     "se_strerror": (ctypes.c_char_p, [_i]),
+    "se_probe_peak": (_i, [_i, ctypes.POINTER(_d)]),
     "se_version": (_i, []),
 }
 

@@ -332,3 +332,15 @@ class Batch:
                                               int(reps), ctypes.byref(best), ctypes.byref(ms)),
                   "se_batch_autotune")
         return best.value, ms.value
+
+
+def probe_peak(kind):
+    """se_probe_peak: measured rate of one GPU unit on the current device
+    (kind: "fp32_fma" or "fp64_fma" in flop/s, "smem_atomic_u32" or
+    "smem_atomic_f32" in shared-memory atomic adds per second)."""
+    kinds = {"fp32_fma": nat.SE_PROBE_FP32_FMA, "fp64_fma": nat.SE_PROBE_FP64_FMA,
+             "smem_atomic_u32": nat.SE_PROBE_SMEM_ATOMIC_U32,
+             "smem_atomic_f32": nat.SE_PROBE_SMEM_ATOMIC_F32}
+    out = ctypes.c_double()
+    nat.check(nat.load().se_probe_peak(kinds[kind], ctypes.byref(out)), "se_probe_peak")
+    return out.value

@@ -68,6 +68,9 @@ def test_argument_validation(lib):
     assert lib.se_plan_destroy(h) == nat.SE_OK
     assert lib.se_plan_destroy(None) == nat.SE_OK
     assert lib.se_strerror(nat.SE_ERR_NONFINITE).decode().startswith("non-finite")
+    out = ctypes.c_double()
+    assert lib.se_probe_peak(9, ctypes.byref(out)) == nat.SE_ERR_ARG
+    assert lib.se_probe_peak(0, None) == nat.SE_ERR_ARG
 
 
 @pytest.mark.parametrize("L,xi,M,P", [(3.0, 3.5, 32, 16), (6.0, 3.12, 52, 6), (10.0, 3.12, 84, 8)])
