@@ -326,6 +326,13 @@ def run_ours(args):
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     roof = roofline(kind, amount, kname, per_launch_ms[dom] / 1e3, prec, peaks, args.workload)
+    roof["measured_unit_peaks"] = {
+        "fp32_fma_tflops": se.probe_peak("fp32_fma") / 1e12,
+        "fp64_fma_tflops": se.probe_peak("fp64_fma") / 1e12,
+        "smem_atomic_u32_gops": se.probe_peak("smem_atomic_u32") / 1e9,
+        "smem_atomic_f32_gops": se.probe_peak("smem_atomic_f32") / 1e9,
+        "hbm_gbs": peaks.get("hbm_gbs"), "source": "se_probe_peak in this run; HBM from "
+        "MEASURED_PEAKS.json"}
     roof["all_kernels"] = {
         work[k][2]: {"us": per_launch_ms[k] * 1e3, "work": work[k][1], "kind": work[k][0]}
         for k in own}
