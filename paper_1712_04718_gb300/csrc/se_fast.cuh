@@ -363,7 +363,7 @@ constexpr int kOverflowBlocks = 8;   // CTAs after the tile CTAs, for the overfl
 // CTA takes the fixed-point scale from the bin kernel's per-block max |q|;
 // CTA 0 also publishes the input checks and the scale for the transform.
 template <int P>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, P <= 8 ? 5 : 1)
 k_fspread(const f4* __restrict__ bucket, int cap, int* __restrict__ tile_count,
           const int* __restrict__ over_idx, int* __restrict__ n_over,
           const f4* __restrict__ wrapped, unsigned long long* __restrict__ g64,

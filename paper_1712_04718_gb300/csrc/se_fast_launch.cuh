@@ -16,6 +16,29 @@ inline int fast_bin_blocks(const KParams<float>& kp) {
     return (int)std::max<long long>(1, std::min<long long>(b, kMaxPartials));
 }
 
+// Dynamic shared memory (at least `need`) with which no more than per_sm CTAs
+// fit on an SM: the SM's shared memory over per_sm + 1/2 CTAs, less the
+// per-CTA reservation and 1 KB for static shared memory.  A grid scheduled
+// early, while its predecessor drains, is otherwise packed onto the SMs that
+// have room; with the cap it spreads over all SMs.
+inline size_t smem_cap_per_sm(size_t need, int per_sm) {
+    int dev = 0, sm_bytes = 0, reserved = 0;
+    if (per_sm < 1 || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess)
+        return need;
+    const long long floor_b = (long long)(sm_bytes / (per_sm + 0.5)) - reserved - 1024;
+    return floor_b > (long long)need ? (size_t)floor_b : need;
+}
+
+inline int sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return n;
+}
+
 template <int P>
 cudaError_t fast_spread_P(const KParams<float>& kp, const FastBufs& b, int nbin, cudaStream_t s) {
     const size_t R = (size_t)kp.tile + P - 1;
@@ -25,10 +48,14 @@ cudaError_t fast_spread_P(const KParams<float>& kp, const FastBufs& b, int nbin,
     cudaError_t e = cudaFuncSetAttribute(k_fspread<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kSmemBudget);
     if (e != cudaSuccess) return e;
-    // an ordinary launch (no early scheduling): the CTAs are then spread over
-    // all SMs instead of being packed onto the SMs that had room during the bin
-    return launch_ex(k_fspread<P>, kp.ntiles + kOverflowBlocks, kThreads, (size_t)slab * plane, s,
-                     false, (const f4*)b.bucket, b.cap, b.tile_count, (const int*)b.over_idx,
+    // scheduled early (dependent launch) with at most ceil(grid / SMs) CTAs
+    // per SM, up to the 5 that the kernel's registers allow
+    const int grid = kp.ntiles + kOverflowBlocks, nsm = sm_count();
+    const int per_sm = nsm > 0 ? (grid + nsm - 1) / nsm : 0;
+    const size_t dyn = (P <= 8 && per_sm >= 1 && per_sm <= 5)
+                           ? smem_cap_per_sm((size_t)slab * plane, per_sm)
+                           : (size_t)slab * plane;
+    return launch_ex(k_fspread<P>, grid, kThreads, dyn, s, true, (const f4*)b.bucket, b.cap, b.tile_count, (const int*)b.over_idx,
                      (int*)(b.tickets + 4), (const f4*)b.wrapped, (unsigned long long*)b.g64, kp,
                      (const double*)b.partials, nbin, b.tickets + 3, b.acc, slab);
 }
