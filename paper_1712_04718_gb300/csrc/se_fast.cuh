@@ -13,8 +13,9 @@
 //   k_slab_fwd  per x-slab: forward DFT along z (real to complex; the
 //               fixed-point grid is converted to float here), then along y
 //   k_xpass     forward DFT along x, scaling by G(k)/M^3 (Eq. 3.6) with the
-//               grid energy, inverse DFT along x
-//   k_slab_inv  per x-slab: inverse DFT along y, then along z (complex to real)
+//               grid energy partials, inverse DFT along x
+//   k_slab_inv  per x-slab: inverse DFT along y, then along z (complex to real);
+//               one more CTA sums the grid energy
 //   (k_gather from se_kernels.cuh reads the real grid)
 //
 // Unsorted variant: k_fdirect replaces k_fbin and k_fspread by
@@ -737,31 +738,22 @@ __device__ __forceinline__ df2 xpass_body(float2* __restrict__ C, const float2* 
 }
 
 #ifndef SE_BATCH_TU
+// Each CTA leaves its grid-energy partial (a double-float pair); the sum is
+// taken by an extra CTA of k_slab_inv, off the critical path.
 __global__ void __launch_bounds__(256)
 k_xpass(float2* __restrict__ C, const float2* __restrict__ tw_g, const float* __restrict__ green,
-        int M, float invM3, double* __restrict__ partials, unsigned* ticket, Acc* acc,
-        double e_scale, double* E_out) {
+        int M, float invM3, double* __restrict__ partials) {
     SE_STAMP(4, 0);
     pdl_wait();
     pdl_launch_next();
     SE_STAMP(4, 1);
-    __shared__ df2 sbuf[32];
     const df2 tot = xpass_body(C, tw_g, green, M, invM3, blockIdx.x);
     float* pf = reinterpret_cast<float*>(partials);
     if (threadIdx.x == 0) {
         pf[2 * blockIdx.x] = tot.hi;
         pf[2 * blockIdx.x + 1] = tot.lo;
     }
-    const bool lastb = last_block(ticket);
     SE_STAMP(4, 5);
-    if (!lastb) return;
-    const df2 sum = sum_partials_df(pf, gridDim.x, 1, 0, sbuf);
-    if (threadIdx.x == 0) {
-        const double e = df_to_double(sum);
-        acc->e_grid = e;
-        if (E_out) *E_out = e_scale * e;
-        *ticket = 0u;
-    }
 }
 #endif  // SE_BATCH_TU
 
@@ -819,13 +811,26 @@ __device__ __forceinline__ void slab_inv_body(const float2* __restrict__ C, floa
 }
 
 #ifndef SE_BATCH_TU
+// CTAs 0..M-1: the inverse slab transforms; CTA M: the grid energy from the
+// x pass's nparts partials (acc->e_grid and, scaled, *E_out).
 __global__ void __launch_bounds__(kSlabThreads)
 k_slab_inv(const float2* __restrict__ C, float* __restrict__ R, const float2* __restrict__ tw_g,
-           int M) {
+           int M, const double* __restrict__ xparts, int nparts, Acc* acc, double e_scale,
+           double* E_out) {
     SE_STAMP(5, 0);
     pdl_wait();
     pdl_launch_next();
     SE_STAMP(5, 1);
+    if ((int)blockIdx.x == M) {
+        __shared__ df2 sbuf[32];
+        const df2 sum = sum_partials_df(reinterpret_cast<const float*>(xparts), nparts, 1, 0, sbuf);
+        if (threadIdx.x == 0) {
+            const double e = df_to_double(sum);
+            acc->e_grid = e;
+            if (E_out) *E_out = e_scale * e;
+        }
+        return;
+    }
     extern __shared__ __align__(16) unsigned char sm[];
     slab_inv_body(C, R, tw_g, M, blockIdx.x, sm);
 }

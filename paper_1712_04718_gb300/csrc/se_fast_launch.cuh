@@ -128,10 +128,11 @@ cudaError_t fast_transform(const KParams<float>& kp, const FastBufs& b, double e
     if (marks) mark(ctx, 3);
     const float invM3 = (float)(1.0 / ((double)M * M * M));
     e = launch_ex(k_xpass, M * nch, kThreads, 0, s, true, C, tw, b.green_f, M, invM3,
-                  b.partials + 5 * kMaxPartials, b.tickets + 1, b.acc, e_scale, E_grid);
+                  b.partials + 5 * kMaxPartials);
     if (e != cudaSuccess) return e;
     if (marks) mark(ctx, 4);
-    e = launch_ex(k_slab_inv, M, kSlabThreads, slab, s, true, (const float2*)C, b.rgrid, tw, M);
+    e = launch_ex(k_slab_inv, M + 1, kSlabThreads, slab, s, true, (const float2*)C, b.rgrid, tw, M,
+                  (const double*)(b.partials + 5 * kMaxPartials), M * nch, b.acc, e_scale, E_grid);
     if (e != cudaSuccess) return e;
     if (marks) mark(ctx, 5);
     return cudaSuccess;

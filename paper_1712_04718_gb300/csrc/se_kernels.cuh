@@ -216,6 +216,33 @@ __device__ __forceinline__ df2 sum_partials_df(const float* partials, int n, int
     return block_sum_df(v, sbuf);
 }
 
+// The same sum by one warp (valid in lane 0): eight loads per lane in flight
+// at a time, then a shuffle reduction; no block barrier.
+__device__ __forceinline__ df2 warp_sum_partials_df(const float* partials, int n, int stride,
+                                                    int offset) {
+    const int lane = threadIdx.x & 31;
+    df2 v = df_from(0.0f);
+    for (int k0 = lane; k0 < n; k0 += 32 * 8) {
+        float hi[8], lo[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int k = k0 + 32 * u;
+            hi[u] = k < n ? __ldcg(partials + 2 * (k * stride + offset)) : 0.0f;
+            lo[u] = k < n ? __ldcg(partials + 2 * (k * stride + offset) + 1) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v = df_add(v, df2{hi[u], lo[u]});
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        df2 u;
+        u.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        u.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        v = df_add(v, u);
+    }
+    return v;
+}
+
 // Last-block detection: every block stores its partial, fences, and takes a
 // ticket; the block with the last ticket sees all partials.
 __device__ __forceinline__ bool last_block(unsigned* ticket) {
@@ -770,8 +797,8 @@ if (threadIdx.x == 0) {
 }
 const bool lastb = last_block(ticket);
 SE_STAMP(6, 5);
-if (!lastb) return;
-const df2 t = sum_partials_df(pf, gridDim.x, 1, 0, sbuf_df);
+if (!lastb || threadIdx.x >= 32) return;
+const df2 t = warp_sum_partials_df(pf, gridDim.x, 1, 0);
 SE_STAMP(6, 6);
 if (threadIdx.x == 0) {
     const double s = df_to_double(t);
