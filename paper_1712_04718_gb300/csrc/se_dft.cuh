@@ -235,20 +235,21 @@ __host__ __device__ inline int dft_split(int M) {
 // factored form with the scratch Z (M x C complex, distinct from X and Y).
 // Called by the whole block; X must be ready (synchronised) before the call,
 // and Y is complete after the caller's next barrier.
+template <int TK = 2, int TC = 2>
 __device__ __forceinline__ void dft_c2c_fact(const float2* __restrict__ X, int xj, int xc,
                                              float2* __restrict__ Y, int yk, int yc, int C,
                                              float2* __restrict__ Z,
                                              const float2* __restrict__ tw, int M, float sign) {
     const int M1 = dft_split(M), M2 = M / M1;
     if (M1 == 1) {
-        dft_stage<2, 2>(X, Y, StageDesc{xj, 0, xc, yk, 0, yc, M, M, C, C, 1, 0}, tw, M, sign);
+        dft_stage<TK, TC>(X, Y, StageDesc{xj, 0, xc, yk, 0, yc, M, M, C, C, 1, 0}, tw, M, sign);
         return;
     }
-    dft_stage<2, 2>(X, Z, StageDesc{M1 * xj, xj, xc, C, M2 * C, 1, M2, M2, M1 * C, C, M1, 1}, tw,
-                    M, sign);
+    dft_stage<TK, TC>(X, Z, StageDesc{M1 * xj, xj, xc, C, M2 * C, 1, M2, M2, M1 * C, C, M1, 1},
+                      tw, M, sign);
     __syncthreads();
-    dft_stage<2, 2>(Z, Y, StageDesc{M2 * C, C, 1, M2 * yk, yk, yc, M1, M1, M2 * C, C, M2, 0}, tw,
-                    M, sign);
+    dft_stage<TK, TC>(Z, Y, StageDesc{M2 * C, C, 1, M2 * yk, yk, yc, M1, M1, M2 * C, C, M2, 0},
+                      tw, M, sign);
 }
 
 }  // namespace se

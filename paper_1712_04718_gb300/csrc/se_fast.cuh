@@ -27,6 +27,8 @@
 // (Cooley-Tukey, two stages), the real-to-complex and complex-to-real ones
 // direct; twiddles e^{-2 pi i r/M} from a table in shared memory.
 #pragma once
+#include <cooperative_groups.h>
+
 #include <type_traits>
 
 #include "se_dft.cuh"
@@ -56,12 +58,33 @@ cudaError_t launch_ex(void (*kern)(KArgs...), int grid, int block, size_t smem, 
     return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
+// The same with a thread-block cluster of csize CTAs along x.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_cluster(void (*kern)(KArgs...), int grid, int block, size_t smem, int csize,
+                           cudaStream_t s, bool pdl, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 2 : 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // ---------------------------------------------------------------------------
 // Tile buckets: particle slot s of tile t lives at bucket[t * cap + s].  The
 // bin kernel takes a slot with an atomic on the tile's count and writes the
 // particle there directly (no scan, no second pass); slots past cap go to an
 // overflow list that the spread kernel adds with global fixed-point atomics
-// (exact integers, so the grid does not depend on which path a particle took).
+// (integer additions: the grid does not depend on their order).
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_fbin(const T* __restrict__ xyz, const T* __restrict__ q, const KParams<T> kp,
@@ -717,7 +740,7 @@ __device__ __forceinline__ df2 xpass_body(float2* __restrict__ C, const float2* 
     }
     __syncthreads();
     SE_STAMP(4, 2);
-    dft_c2c_fact(s, kFastKC, 1, s2, kFastKC, 1, nc, s3, tw, M, -1.0f);
+    dft_c2c_fact<1, 2>(s, kFastKC, 1, s2, kFastKC, 1, nc, s3, tw, M, -1.0f);
     __syncthreads();
     SE_STAMP(4, 3);
     df2 en = df_from(0.0f);   // double-float energy sum
@@ -732,7 +755,7 @@ __device__ __forceinline__ df2 xpass_body(float2* __restrict__ C, const float2* 
         s2[kx * kFastKC + kk] = make_float2(v.x * f, v.y * f);
     }
     __syncthreads();
-    dft_c2c_fact(s2, kFastKC, 1, C + (size_t)y * Mh + c0, M * Mh, 1, nc, s3, tw, M, 1.0f);
+    dft_c2c_fact<1, 2>(s2, kFastKC, 1, C + (size_t)y * Mh + c0, M * Mh, 1, nc, s3, tw, M, 1.0f);
     SE_STAMP(4, 4);
     return block_sum_df(en, sbuf);
 }
@@ -833,6 +856,209 @@ k_slab_inv(const float2* __restrict__ C, float* __restrict__ R, const float2* __
     }
     extern __shared__ __align__(16) unsigned char sm[];
     slab_inv_body(C, R, tw_g, M, blockIdx.x, sm);
+}
+#endif  // SE_BATCH_TU
+
+// ---------------------------------------------------------------------------
+// Slab transforms on 2-CTA thread-block clusters (single system): the two
+// CTAs of a cluster share one x-slab, so that the transforms run on twice the
+// SMs.  Forward: each CTA transforms half of the y rows along z and writes
+// each result column straight into the shared memory of the CTA that owns
+// that kz column (distributed shared memory stores), then, after one cluster
+// barrier, transforms its kz columns along y.  Inverse: the same in the
+// opposite order, with the Hermitian weights of the z real transform applied
+// when the spectrum is loaded.
+
+constexpr int kSlabCL = 2;
+// register tiles of the half-slab transforms (outputs x columns per thread):
+// the forward one has too few outputs to give every thread a 2 x 2 tile;
+// the inverse measured faster with 2 x 2
+constexpr int kClTK = 1, kClTC = 2, kClInvTK = 2, kClInvTC = 2;
+
+struct SlabClLayout {
+    int ry, kc;                       // y rows and kz columns per CTA
+    size_t tw, a, b, c, d, total;     // byte offsets of the regions
+};
+
+// forward: tw | S: ry x (M+1) floats | T: Mh x ry complex | X: kc x M complex
+//          (written by both CTAs) | Z: kc x M complex (factored-DFT scratch)
+// inverse: tw | A: M x kc complex | Z: M x kc complex | T: kc x (M+1) complex
+//          | X: Mh x ry complex (written by both CTAs) | S: ry x (M+1) floats
+__host__ __device__ inline SlabClLayout slabcl_layout(int M) {
+    SlabClLayout l;
+    const size_t Mh = M / 2 + 1, SP = M + 1;
+    l.ry = (M + kSlabCL - 1) / kSlabCL;
+    l.kc = (int)((Mh + kSlabCL - 1) / kSlabCL);
+    auto up = [](size_t v) { return (v + 15) / 16 * 16; };
+    const size_t f2 = sizeof(float2);
+    const size_t r1 = up((size_t)l.ry * SP * sizeof(float));          // S
+    const size_t r2 = up(Mh * l.ry * f2);                             // T (fwd) / X (inv)
+    const size_t r3 = up((size_t)l.kc * M * f2);                      // X, Z (fwd) / A, Z (inv)
+    const size_t r4 = up((size_t)l.kc * SP * f2);                     // T (inv)
+    l.tw = 0;
+    l.a = up((size_t)M * f2);
+    l.b = l.a + (r1 > r3 ? r1 : r3);
+    l.c = l.b + (r2 > r3 ? r2 : r3);
+    l.d = l.c + (r3 > r4 ? r3 : r4);
+    l.total = l.d + (r3 > r2 ? r3 : r2) + (r1 > r3 ? r1 : r3);
+    return l;
+}
+
+#ifndef SE_BATCH_TU
+__global__ void __launch_bounds__(kSlabThreads)
+k_slab_fwd_cl(const long long* __restrict__ g64, float2* __restrict__ Cg,
+              const float2* __restrict__ tw_g, int M, const Acc* __restrict__ acc) {
+    namespace cg = cooperative_groups;
+    SE_STAMP(3, 0);
+    pdl_wait();
+    pdl_launch_next();
+    SE_STAMP(3, 1);
+    extern __shared__ __align__(16) unsigned char sm[];
+    cg::cluster_group clu = cg::this_cluster();
+    const int rank = (int)clu.block_rank(), x = blockIdx.x / kSlabCL;
+    const SlabClLayout l = slabcl_layout(M);
+    const int Mh = M / 2 + 1, SP = M + 1;
+    float2* tw = reinterpret_cast<float2*>(sm + l.tw);
+    float* S = reinterpret_cast<float*>(sm + l.a);
+    float2* T = reinterpret_cast<float2*>(sm + l.b);
+    float2* X = reinterpret_cast<float2*>(sm + l.c);
+    float2* Z = reinterpret_cast<float2*>(sm + l.d);
+    const int y0 = rank * l.ry, ny = max(0, min(l.ry, M - y0));
+    const int k0 = rank * l.kc, nk = max(0, min(l.kc, Mh - k0));
+    load_twiddles(tw, tw_g, M);
+    const float inv = acc->fx_inv;
+    const FDiv fM = fdiv_of(M);
+    const long long* src = g64 + ((size_t)x * M + y0) * M;
+    for (int e0 = threadIdx.x; e0 < ny * M; e0 += blockDim.x * kLoadBatch) {
+        long long v[kLoadBatch];
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int e = e0 + u * (int)blockDim.x;
+            v[u] = e < ny * M ? src[e] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int e = e0 + u * (int)blockDim.x;
+            if (e >= ny * M) break;
+            const int yl = fdiv(e, fM), z = e - yl * M;
+            const unsigned long long w = (unsigned long long)v[u];
+            const float hi = (float)(int)(w >> 32), lo = (float)(unsigned)(w & 0xffffffffull);
+            S[yl * SP + z] = fmaf(hi, 4294967296.0f, lo) * inv;
+        }
+    }
+    __syncthreads();
+    SE_STAMP(3, 2);
+    // z, real to complex, own rows: X(j = z, c = yl) = S[yl][z]  ->  T[kz][yl]
+    dft_r2c<kClTK, kClTC>(S, 1, SP, T, l.ry, 1, M, Mh, ny, tw, M);
+    __syncthreads();
+    // push: kz column k of these rows goes to the CTA owning k, X[k - k0'][y0 + yl]
+    {
+        float2* Xr[kSlabCL];
+#pragma unroll
+        for (int r = 0; r < kSlabCL; ++r) Xr[r] = clu.map_shared_rank(X, r);
+        const FDiv fny = fdiv_of(max(ny, 1));
+        for (int e = threadIdx.x; e < Mh * ny; e += blockDim.x) {
+            const int kz = fdiv(e, fny), yl = e - kz * ny;
+            const int owner = kz >= l.kc ? 1 : 0;
+            Xr[owner][(kz - owner * l.kc) * M + y0 + yl] = T[kz * l.ry + yl];
+        }
+    }
+    clu.sync();   // every push has landed; no shared memory is read remotely afterwards
+    SE_STAMP(3, 3);
+    // y forward: X(j = y, c = kl)  ->  C[x][ky][k0 + kl]
+    dft_c2c_fact<kClTK, kClTC>(X, 1, M, Cg + (size_t)x * M * Mh + k0, Mh, 1, nk, Z, tw, M, -1.0f);
+    SE_STAMP(3, 4);
+}
+
+// Clusters 0..M-1: inverse slab transforms; cluster M: the grid energy from
+// the x pass's nparts partials (acc->e_grid and, scaled, *E_out).
+__global__ void __launch_bounds__(kSlabThreads)
+k_slab_inv_cl(const float2* __restrict__ Cg, float* __restrict__ R, const float2* __restrict__ tw_g,
+              int M, const double* __restrict__ xparts, int nparts, Acc* acc, double e_scale,
+              double* E_out) {
+    namespace cg = cooperative_groups;
+    SE_STAMP(5, 0);
+    pdl_wait();
+    pdl_launch_next();
+    SE_STAMP(5, 1);
+    const int x = blockIdx.x / kSlabCL;
+    if (x == M) {   // the whole cluster takes this branch
+        if (blockIdx.x % kSlabCL != 0) return;
+        __shared__ df2 sbuf[32];
+        const df2 sum = sum_partials_df(reinterpret_cast<const float*>(xparts), nparts, 1, 0, sbuf);
+        if (threadIdx.x == 0) {
+            const double e = df_to_double(sum);
+            acc->e_grid = e;
+            if (E_out) *E_out = e_scale * e;
+        }
+        return;
+    }
+    extern __shared__ __align__(16) unsigned char sm[];
+    cg::cluster_group clu = cg::this_cluster();
+    const int rank = (int)clu.block_rank();
+    const SlabClLayout l = slabcl_layout(M);
+    const int Mh = M / 2 + 1, SP = M + 1;
+    float2* tw = reinterpret_cast<float2*>(sm + l.tw);
+    float2* A = reinterpret_cast<float2*>(sm + l.a);
+    float2* Z = reinterpret_cast<float2*>(sm + l.b);
+    float2* T = reinterpret_cast<float2*>(sm + l.c);
+    float2* X = reinterpret_cast<float2*>(sm + l.d);
+    float* S = reinterpret_cast<float*>(sm + l.a);   // A is dead by then
+    const int y0 = rank * l.ry, ny = max(0, min(l.ry, M - y0));
+    const int k0 = rank * l.kc, nk = max(0, min(l.kc, Mh - k0));
+    load_twiddles(tw, tw_g, M);
+    const FDiv fnk = fdiv_of(max(nk, 1)), fM = fdiv_of(M);
+    // own kz columns of the slab, times the Hermitian weights (1 at kz = 0
+    // and M/2, else 2): A[ky][kl]
+    const float2* src = Cg + (size_t)x * M * Mh + k0;
+    for (int e0 = threadIdx.x; e0 < M * nk; e0 += blockDim.x * kLoadBatch) {
+        float2 v[kLoadBatch];
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int e = e0 + u * (int)blockDim.x;
+            if (e < M * nk) {
+                const int ky = fdiv(e, fnk), kl = e - ky * nk;
+                v[u] = src[(size_t)ky * Mh + kl];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int e = e0 + u * (int)blockDim.x;
+            if (e < M * nk) {
+                const int ky = fdiv(e, fnk), kl = e - ky * nk;
+                const int kz = k0 + kl;
+                const float wgt = (kz == 0 || 2 * kz == M) ? 1.0f : 2.0f;
+                A[ky * l.kc + kl] = make_float2(wgt * v[u].x, wgt * v[u].y);
+            }
+        }
+    }
+    __syncthreads();
+    SE_STAMP(5, 2);
+    // y inverse: X(j = ky, c = kl) = A[ky][kl]  ->  T[kl][y]
+    dft_c2c_fact<kClInvTK, kClInvTC>(A, l.kc, 1, T, 1, SP, nk, Z, tw, M, 1.0f);
+    __syncthreads();
+    // push: row y of these kz columns goes to the CTA owning y, X[k0 + kl][y - y0']
+    {
+        float2* Xr[kSlabCL];
+#pragma unroll
+        for (int r = 0; r < kSlabCL; ++r) Xr[r] = clu.map_shared_rank(X, r);
+        for (int e = threadIdx.x; e < nk * M; e += blockDim.x) {
+            const int kl = fdiv(e, fM), y = e - kl * M;
+            const int owner = y >= l.ry ? 1 : 0;
+            Xr[owner][(k0 + kl) * l.ry + (y - owner * l.ry)] = T[kl * SP + y];
+        }
+    }
+    clu.sync();   // every push has landed; no shared memory is read remotely afterwards
+    // z complex to real, own rows: X(j = kz, c = yl) = X[kz][yl]  ->  S[yl][z]
+    dft_c2r<kClInvTK, kClInvTC>(X, l.ry, 1, S, 1, SP, Mh, M, ny, tw, M);
+    __syncthreads();
+    SE_STAMP(5, 3);
+    float* dst = R + ((size_t)x * M + y0) * M;
+    for (int e = threadIdx.x; e < ny * M; e += blockDim.x) {
+        const int yl = fdiv(e, fM), z = e - yl * M;
+        dst[e] = S[yl * SP + z];
+    }
+    SE_STAMP(5, 4);
 }
 #endif  // SE_BATCH_TU
 

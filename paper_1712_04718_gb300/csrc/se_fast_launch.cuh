@@ -109,20 +109,23 @@ cudaError_t fast_transform(const KParams<float>& kp, const FastBufs& b, double e
     const int nch = (Mh + kFastKC - 1) / kFastKC;
     const float2* tw = (const float2*)b.tw;
     float2* C = (float2*)b.cgrid;
-    // at least half an SM's shared memory: one slab CTA per SM, whatever else
-    // is resident when the grid is scheduled early
-    const size_t slab = std::max(slab_smem_bytes(M), kSlabSmemFloor);
-    cudaError_t e = cudaFuncSetAttribute(k_slab_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_slab_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab);
-    if (e != cudaSuccess) return e;
+    const int nsm = sm_count();
+    cudaError_t e;
     if (b.unsorted) {
+        // at least half an SM's shared memory: one slab CTA per SM, whatever
+        // else is resident when the grid is scheduled early
+        const size_t slab = std::max(slab_smem_bytes(M), kSlabSmemFloor);
         e = cudaFuncSetAttribute(k_slab_fwd_f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab);
         if (e != cudaSuccess) return e;
         e = launch_ex(k_slab_fwd_f, M, kSlabThreads, slab, s, true, (float*)b.g64, C, tw, M);
     } else {
-        e = launch_ex(k_slab_fwd, M, kSlabThreads, slab, s, true, (const long long*)b.g64, C, tw,
-                      M, (const Acc*)b.acc);
+        // 2-CTA clusters per x-slab, at most ceil(2M / SMs) CTAs per SM
+        const int per_sm = nsm > 0 ? (kSlabCL * M + nsm - 1) / nsm : 1;
+        const size_t cl = smem_cap_per_sm(slabcl_layout(M).total, per_sm);
+        e = cudaFuncSetAttribute(k_slab_fwd_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cl);
+        if (e != cudaSuccess) return e;
+        e = launch_cluster(k_slab_fwd_cl, kSlabCL * M, kSlabThreads, cl, kSlabCL, s, true,
+                           (const long long*)b.g64, C, tw, M, (const Acc*)b.acc);
     }
     if (e != cudaSuccess) return e;
     if (marks) mark(ctx, 3);
@@ -131,8 +134,16 @@ cudaError_t fast_transform(const KParams<float>& kp, const FastBufs& b, double e
                   b.partials + 5 * kMaxPartials);
     if (e != cudaSuccess) return e;
     if (marks) mark(ctx, 4);
-    e = launch_ex(k_slab_inv, M + 1, kSlabThreads, slab, s, true, (const float2*)C, b.rgrid, tw, M,
-                  (const double*)(b.partials + 5 * kMaxPartials), M * nch, b.acc, e_scale, E_grid);
+    {
+        const int per_sm = nsm > 0 ? (kSlabCL * (M + 1) + nsm - 1) / nsm : 1;
+        const size_t cl = smem_cap_per_sm(slabcl_layout(M).total, per_sm);
+        e = cudaFuncSetAttribute(k_slab_inv_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cl);
+        if (e != cudaSuccess) return e;
+        e = launch_cluster(k_slab_inv_cl, kSlabCL * (M + 1), kSlabThreads, cl, kSlabCL, s, true,
+                           (const float2*)C, b.rgrid, tw, M,
+                           (const double*)(b.partials + 5 * kMaxPartials), M * nch, b.acc, e_scale,
+                           E_grid);
+    }
     if (e != cudaSuccess) return e;
     if (marks) mark(ctx, 5);
     return cudaSuccess;
