@@ -150,6 +150,8 @@ k_fbin(const T* __restrict__ xyz, const T* __restrict__ q, const KParams<T> kp,
         pf[6 * blockIdx.x + 3] = r1.lo;
         pf[6 * blockIdx.x + 4] = __int_as_float(sbad);
         pf[6 * blockIdx.x + 5] = __uint_as_float(smax);
+        // the same maximum in a contiguous array, which every spread CTA reads
+        reinterpret_cast<unsigned*>(partials + 3 * kMaxPartials)[blockIdx.x] = smax;
     }
     SE_STAMP(0, 4);
 }
@@ -242,10 +244,13 @@ __device__ __forceinline__ void fx_split(float v, unsigned* vh, unsigned* vl) {
 // Integer additions: the grid does not depend on their order.  Called by one
 // whole block (uniformly: the early return is per block).
 template <int P>
+// zeroed: the caller has cleared the first slab's region already; first:
+// if non-null, this thread's group's first particle, loaded by the caller.
 __device__ __forceinline__ void spread_tile(const f4* __restrict__ parts, int n,
                                             unsigned long long* __restrict__ g64,
                                             const KParams<float>& kp, float fxs, int slab,
-                                            int tile, unsigned* acc, float* sE3) {
+                                            int tile, unsigned* acc, float* sE3,
+                                            bool zeroed = false, const f4* first = nullptr) {
     constexpr int D = pick_d(P), G = P / D, GPW = 32 / G;
     if (n <= 0) return;
     if (threadIdx.x < P) sE3[threadIdx.x] = kp.E3[threadIdx.x];
@@ -267,12 +272,15 @@ __device__ __forceinline__ void spread_tile(const f4* __restrict__ parts, int n,
     for (int s0 = 0; s0 < Rx; s0 += slab) {
         const int ns = min(slab, Rx - s0);
         const int nel = ns * plane;
-        for (int e = threadIdx.x; e < nel; e += blockDim.x) acc[e] = 0u;
+        if (!(zeroed && s0 == 0))
+            for (int e = threadIdx.x; e < nel; e += blockDim.x) acc[e] = 0u;
         __syncthreads();
         SE_STAMP(2, 2);
         if (act) {
             for (int p = group; p < n; p += ngroups) {
-                const f4 v = parts[p];
+                f4 v;
+                if (first && p == group) v = *first;
+                else v = parts[p];
                 float t;
                 const int cx = cell_of(v.x, kp.invh, M, &t);
                 const float ux = centre_offset(t, cx);
@@ -394,24 +402,42 @@ k_fspread(const f4* __restrict__ bucket, int cap, int* __restrict__ tile_count,
           const KParams<float> kp, const double* __restrict__ partials, int nbin,
           unsigned* ticket, Acc* __restrict__ acc, int slab) {
     SE_STAMP(2, 0);
-    pdl_wait();
-    pdl_launch_next();
-    SE_STAMP(2, 1);
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned* sacc = reinterpret_cast<unsigned*>(smem_raw);
     __shared__ float sE3[P];
     __shared__ float s_fxs;
     __shared__ int s_n;
-    __shared__ df2 sbuf[32];
     __shared__ unsigned s_qm;
-    const float* pf = reinterpret_cast<const float*>(partials);
+    __shared__ df2 sbuf[32];
     const int tile = blockIdx.x;
-    // one round trip: max |q| of the bin blocks, this CTA's particle count
+    // before the bin's results are needed: clear the first slab of this
+    // tile's region and stage the Gaussian table (the CTA is scheduled early)
+    if (tile < kp.ntiles) {
+        const int nT = kp.nT, TT = kp.tile;
+        const int ty = (tile / nT) % nT, tz = tile % nT, tx = tile / (nT * nT);
+        const int plane = (min(TT, kp.M - ty * TT) + P - 1) * (min(TT, kp.M - tz * TT) + P - 1);
+        const int nel = min(slab, min(TT, kp.M - tx * TT) + P - 1) * plane;
+        for (int e = threadIdx.x; e < nel; e += blockDim.x) sacc[e] = 0u;
+    }
+    if (threadIdx.x < P) sE3[threadIdx.x] = kp.E3[threadIdx.x];
     if (threadIdx.x == 0) s_qm = 0u;
+    pdl_wait();
+    pdl_launch_next();
+    SE_STAMP(2, 1);
+    const float* pf = reinterpret_cast<const float*>(partials);
+    // one round trip: max |q| of the bin blocks, this CTA's particle count,
+    // and (speculatively: a bucket slot is always valid memory) the first
+    // particle of this thread's group
+    constexpr int G = P / pick_d(P), GPW = 32 / G;
+    const int group = (threadIdx.x >> 5) * GPW + (threadIdx.x & 31) / G;
+    f4 first;
+    first.x = first.y = first.z = first.w = 0.f;
+    if (tile < kp.ntiles && group < cap) first = bucket[(size_t)tile * cap + group];
     unsigned m = 0u;
-    for (int b = threadIdx.x; b < nbin; b += blockDim.x) m = max(m, __float_as_uint(__ldcg(pf + 6 * b + 5)));
+    const unsigned* qmax_b = reinterpret_cast<const unsigned*>(partials + 3 * kMaxPartials);
+    for (int b = threadIdx.x; b < nbin; b += blockDim.x) m = max(m, __ldcg(qmax_b + b));
     int cnt = 0;
     if (threadIdx.x == blockDim.x - 1) cnt = tile < kp.ntiles ? __ldcg(tile_count + tile) : __ldcg(n_over);
-    if (threadIdx.x < P) sE3[threadIdx.x] = kp.E3[threadIdx.x];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     __syncthreads();
@@ -456,14 +482,15 @@ k_fspread(const f4* __restrict__ bucket, int cap, int* __restrict__ tile_count,
     const float fxs = s_fxs;
     const int n = s_n;
     if (tile < kp.ntiles) {
-        spread_tile<P>(bucket + (size_t)tile * cap, n, g64, kp, fxs, slab, tile,
-                       reinterpret_cast<unsigned*>(smem_raw), sE3);
+        spread_tile<P>(bucket + (size_t)tile * cap, n, g64, kp, fxs, slab, tile, sacc, sE3, true,
+                       &first);
         return;
     }
-    constexpr int D = pick_d(P), G = P / D, GPW = 32 / G;
+    constexpr int D = pick_d(P);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gi = lane / G, k = lane - gi * G;
     const int ngroups = kOverflowBlocks * (blockDim.x >> 5) * GPW;
+    (void)D;
     if (gi < GPW) {
         for (int o = ((blockIdx.x - kp.ntiles) * (blockDim.x >> 5) + warp) * GPW + gi; o < n;
              o += ngroups)

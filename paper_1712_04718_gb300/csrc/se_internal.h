@@ -88,7 +88,8 @@ struct FastBufs {
     int cap;              // bucket capacity
     int* over_idx;        // [N] particles that found their bucket full
     void* wrapped;        // f4 [N]: wrapped (x, y, z, q) in input order, for the gather
-    double* partials;     // bin: [0, 3*1024); x pass: [5*1024, 7*1024)
+    double* partials;     // bin: [0, 3*1024), its max |q| per block as words at [3*1024, ...);
+                          // gather: [4*1024, 5*1024); x pass: [5*1024, 7*1024)
     unsigned* tickets;    // [0] unsorted spread, [1] x pass, [2] gather, [3] overflow
                           // CTAs, [4] overflow count
     Acc* acc;
