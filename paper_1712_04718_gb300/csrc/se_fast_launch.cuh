@@ -111,13 +111,24 @@ cudaError_t fast_transform(const KParams<float>& kp, const FastBufs& b, double e
     float2* C = (float2*)b.cgrid;
     const int nsm = sm_count();
     cudaError_t e;
-    if (b.unsorted) {
-        // at least half an SM's shared memory: one slab CTA per SM, whatever
-        // else is resident when the grid is scheduled early
-        const size_t slab = std::max(slab_smem_bytes(M), kSlabSmemFloor);
-        e = cudaFuncSetAttribute(k_slab_fwd_f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab);
-        if (e != cudaSuccess) return e;
-        e = launch_ex(k_slab_fwd_f, M, kSlabThreads, slab, s, true, (float*)b.g64, C, tw, M);
+    // 2-CTA clusters per x-slab when every CTA gets an SM of its own;
+    // otherwise one CTA per slab (a cap of two CTAs per SM would let an early
+    // placement pack them onto half the SMs)
+    const bool clusters = nsm > 0 && kSlabCL * (M + 1) <= nsm;
+    // at least half an SM's shared memory: one slab CTA per SM, whatever else
+    // is resident when the grid is scheduled early
+    const size_t slab = std::max(slab_smem_bytes(M), kSlabSmemFloor);
+    if (b.unsorted || !clusters) {
+        if (b.unsorted) {
+            e = cudaFuncSetAttribute(k_slab_fwd_f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab);
+            if (e != cudaSuccess) return e;
+            e = launch_ex(k_slab_fwd_f, M, kSlabThreads, slab, s, true, (float*)b.g64, C, tw, M);
+        } else {
+            e = cudaFuncSetAttribute(k_slab_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab);
+            if (e != cudaSuccess) return e;
+            e = launch_ex(k_slab_fwd, M, kSlabThreads, slab, s, true, (const long long*)b.g64, C, tw,
+                          M, (const Acc*)b.acc);
+        }
     } else {
         // 2-CTA clusters per x-slab, at most ceil(2M / SMs) CTAs per SM
         const int per_sm = nsm > 0 ? (kSlabCL * M + nsm - 1) / nsm : 1;
@@ -134,7 +145,12 @@ cudaError_t fast_transform(const KParams<float>& kp, const FastBufs& b, double e
                   b.partials + 5 * kMaxPartials);
     if (e != cudaSuccess) return e;
     if (marks) mark(ctx, 4);
-    {
+    if (!clusters) {
+        e = cudaFuncSetAttribute(k_slab_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab);
+        if (e != cudaSuccess) return e;
+        e = launch_ex(k_slab_inv, M + 1, kSlabThreads, slab, s, true, (const float2*)C, b.rgrid, tw, M,
+                      (const double*)(b.partials + 5 * kMaxPartials), M * nch, b.acc, e_scale, E_grid);
+    } else {
         const int per_sm = nsm > 0 ? (kSlabCL * (M + 1) + nsm - 1) / nsm : 1;
         const size_t cl = smem_cap_per_sm(slabcl_layout(M).total, per_sm);
         e = cudaFuncSetAttribute(k_slab_inv_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cl);
