@@ -11,11 +11,13 @@
 //               of the additions; a few more CTAs add the overflow list with
 //               global 64-bit atomics
 //   k_slab_fwd  per x-slab: forward DFT along z (real to complex; the
-//               fixed-point grid is converted to float here), then along y
+//               fixed-point grid is converted to float here), then along y;
+//               k_slab_fwd_cl the same on a 2-CTA cluster per slab
 //   k_xpass     forward DFT along x, scaling by G(k)/M^3 (Eq. 3.6) with the
 //               grid energy partials, inverse DFT along x
 //   k_slab_inv  per x-slab: inverse DFT along y, then along z (complex to real);
-//               one more CTA sums the grid energy
+//               one more CTA sums the grid energy; k_slab_inv_cl the same on a
+//               2-CTA cluster per slab
 //   (k_gather from se_kernels.cuh reads the real grid)
 //
 // Unsorted variant: k_fdirect replaces k_fbin and k_fspread by

@@ -742,80 +742,80 @@ k_gather(const v4_t<T>* __restrict__ sorted, const int* __restrict__ perm,
     double e_loc = 0.0;
     df2 e_df = df_from(0.0f);
     for (; pb < kp.N; pb += gridDim.x * gpb) {
-const int p = pb + gi;
-const bool valid = (gi < GPW) && (p < kp.N);
-T vphi = T(0), vfx = T(0), vfy = T(0), vfz = T(0);
-if (valid) {
-    if (pb != blockIdx.x * gpb + warp * GPW) {   // later particles: after the wait
-        const v4_t<T> v = sorted[p];
-        qq = v.w;
-        gather_prep<T, P>(v, kp, k, g);
-    }
-    gather_accum<T, P>(g, grid, kp, sE3, vphi, vfx, vfy, vfz);
-}
-SE_STAMP(6, 2);
-// reduce over the G lanes of each particle (lane 0 of the group ends with the sum)
+        const int p = pb + gi;
+        const bool valid = (gi < GPW) && (p < kp.N);
+        T vphi = T(0), vfx = T(0), vfy = T(0), vfz = T(0);
+        if (valid) {
+            if (pb != blockIdx.x * gpb + warp * GPW) {   // later particles: after the wait
+                const v4_t<T> v = sorted[p];
+                qq = v.w;
+                gather_prep<T, P>(v, kp, k, g);
+            }
+            gather_accum<T, P>(g, grid, kp, sE3, vphi, vfx, vfy, vfz);
+        }
+        SE_STAMP(6, 2);
+        // reduce over the G lanes of each particle (lane 0 of the group ends with the sum)
 #pragma unroll
-for (int o = 1; o < G; o <<= 1) {
-    const T a0 = __shfl_down_sync(0xffffffffu, vphi, o);
-    const T a1 = __shfl_down_sync(0xffffffffu, vfx, o);
-    const T a2 = __shfl_down_sync(0xffffffffu, vfy, o);
-    const T a3 = __shfl_down_sync(0xffffffffu, vfz, o);
-    if (k + o < G) {
-        vphi += a0;
-        vfx += a1;
-        vfy += a2;
-        vfz += a3;
-    }
-}
-if (valid && k == 0) {
-    const T ph = vphi * kp.phi_scale;
-    const T fs = qq * kp.F_scale;
-    const int orig = perm ? perm[p] : p;   // no perm: particles in input order
-    if (phi) phi[orig] = ph * phi_mul;
-    if (F) {
-        const T fm = fs * F_mul;
-        F[3 * orig] = fm * vfx;
-        F[3 * orig + 1] = fm * vfy;
-        F[3 * orig + 2] = fm * vfz;
-    }
-    if (kSingle)
-        e_df = df_add(e_df, df_from((float)(qq * ph)));
-    else
-        e_loc += (double)qq * (double)ph;
-}
+        for (int o = 1; o < G; o <<= 1) {
+            const T a0 = __shfl_down_sync(0xffffffffu, vphi, o);
+            const T a1 = __shfl_down_sync(0xffffffffu, vfx, o);
+            const T a2 = __shfl_down_sync(0xffffffffu, vfy, o);
+            const T a3 = __shfl_down_sync(0xffffffffu, vfz, o);
+            if (k + o < G) {
+                vphi += a0;
+                vfx += a1;
+                vfy += a2;
+                vfz += a3;
+            }
+        }
+        if (valid && k == 0) {
+            const T ph = vphi * kp.phi_scale;
+            const T fs = qq * kp.F_scale;
+            const int orig = perm ? perm[p] : p;   // no perm: particles in input order
+            if (phi) phi[orig] = ph * phi_mul;
+            if (F) {
+                const T fm = fs * F_mul;
+                F[3 * orig] = fm * vfx;
+                F[3 * orig + 1] = fm * vfy;
+                F[3 * orig + 2] = fm * vfz;
+            }
+            if (kSingle)
+                e_df = df_add(e_df, df_from((float)(qq * ph)));
+            else
+                e_loc += (double)qq * (double)ph;
+        }
     }
     SE_STAMP(6, 3);
     if (kSingle) {
-// double-float partials: (hi, lo) floats per block
-float* pf = reinterpret_cast<float*>(partials);
-const df2 r = block_sum_df(e_df, sbuf_df);
-SE_STAMP(6, 4);
-if (threadIdx.x == 0) {
-    pf[2 * blockIdx.x] = r.hi;
-    pf[2 * blockIdx.x + 1] = r.lo;
-}
-const bool lastb = last_block(ticket);
-SE_STAMP(6, 5);
-if (!lastb || threadIdx.x >= 32) return;
-const df2 t = warp_sum_partials_df(pf, gridDim.x, 1, 0);
-SE_STAMP(6, 6);
-if (threadIdx.x == 0) {
-    const double s = df_to_double(t);
-    acc->e_gather = s;
-    if (E_out) *E_out = e_scale * s;
-    *ticket = 0u;
-}
-return;
+        // double-float partials: (hi, lo) floats per block
+        float* pf = reinterpret_cast<float*>(partials);
+        const df2 r = block_sum_df(e_df, sbuf_df);
+        SE_STAMP(6, 4);
+        if (threadIdx.x == 0) {
+            pf[2 * blockIdx.x] = r.hi;
+            pf[2 * blockIdx.x + 1] = r.lo;
+        }
+        const bool lastb = last_block(ticket);
+        SE_STAMP(6, 5);
+        if (!lastb || threadIdx.x >= 32) return;
+        const df2 t = warp_sum_partials_df(pf, gridDim.x, 1, 0);
+        SE_STAMP(6, 6);
+        if (threadIdx.x == 0) {
+            const double s = df_to_double(t);
+            acc->e_gather = s;
+            if (E_out) *E_out = e_scale * s;
+            *ticket = 0u;
+        }
+        return;
     }
     double r = block_sum(e_loc, sbuf);
     if (threadIdx.x == 0) partials[blockIdx.x] = r;
     if (!last_block(ticket)) return;
     const double s = sum_partials(partials, gridDim.x, 1, 0, sbuf);
     if (threadIdx.x == 0) {
-acc->e_gather = s;
-if (E_out) *E_out = e_scale * s;
-*ticket = 0u;
+        acc->e_gather = s;
+        if (E_out) *E_out = e_scale * s;
+        *ticket = 0u;
     }
 }
 
