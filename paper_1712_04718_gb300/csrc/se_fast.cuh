@@ -90,8 +90,8 @@ cudaError_t launch_cluster(void (*kern)(KArgs...), int grid, int block, size_t s
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_fbin(const T* __restrict__ xyz, const T* __restrict__ q, const KParams<T> kp,
-       int* __restrict__ tile_count, v4_t<T>* __restrict__ bucket, int cap,
-       int* __restrict__ over_idx, int* __restrict__ n_over, v4_t<T>* __restrict__ wrapped,
+       int* __restrict__ tile_count, v4_t<T>* __restrict__ bucket, int* __restrict__ bucket_idx,
+       int cap, int* __restrict__ over_idx, int* __restrict__ n_over, v4_t<T>* __restrict__ wrapped,
        double* __restrict__ partials, long long* __restrict__ g64) {
     SE_STAMP(0, 0);
     pdl_wait();
@@ -124,6 +124,7 @@ k_fbin(const T* __restrict__ xyz, const T* __restrict__ q, const KParams<T> kp,
         const int s = atomicAdd(tile_count + tile, 1);
         if (s < cap) {
             bucket[(size_t)tile * cap + s] = v;
+            bucket_idx[(size_t)tile * cap + s] = i;
         } else {
             const int o = atomicAdd(n_over, 1);
             if (o < kp.N) over_idx[o] = i;
@@ -399,7 +400,7 @@ constexpr int kOverflowBlocks = 8;   // CTAs after the tile CTAs, for the overfl
 template <int P>
 __global__ void __launch_bounds__(256, P <= 8 ? 5 : 1)
 k_fspread(const f4* __restrict__ bucket, int cap, int* __restrict__ tile_count,
-          const int* __restrict__ over_idx, int* __restrict__ n_over,
+          int* __restrict__ tile_n, const int* __restrict__ over_idx, int* __restrict__ n_over,
           const f4* __restrict__ wrapped, unsigned long long* __restrict__ g64,
           const KParams<float> kp, const double* __restrict__ partials, int nbin,
           unsigned* ticket, Acc* __restrict__ acc, int slab) {
@@ -451,6 +452,7 @@ k_fspread(const f4* __restrict__ bucket, int cap, int* __restrict__ tile_count,
         } else {
             s_n = min(cnt, kp.N);
         }
+        tile_n[min(tile, kp.ntiles)] = s_n;   // kept for the tile gather
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -505,6 +507,261 @@ k_fspread(const f4* __restrict__ bucket, int cap, int* __restrict__ tile_count,
             *n_over = 0;
             *ticket = 0u;
         }
+    }
+}
+
+// Gather (Eq. 3.9, Sec. 3.1) by tiles, for tiles that hold many particles:
+// CTA t copies the real grid over tile t's region (the P-point supports of
+// every particle of the tile) into shared memory once, then gathers the
+// tile's bucket from it, with the arithmetic of k_gather in the same order;
+// the last kOverflowBlocks CTAs gather the overflow list from the global
+// grid.  The particles' factors are computed before the dependent-launch
+// wait.  Outputs go to the particles' input positions; the energy
+// 1/2 sum q phi is reduced as in k_gather.
+template <int P>
+struct TilePrep {
+    static constexpr int D = pick_d(P);
+    float gy[P], dgy[P], gz[D], dgz[D];
+    float ux, px0, Bx, q;
+    int base;   // region offset of support point (0, 0, this lane's first z)
+};
+
+template <int P>
+__device__ __forceinline__ void tile_prep(const f4& v, const KParams<float>& kp, int k, int t0x,
+                                          int t0y, int t0z, int Ry, int Rz, TilePrep<P>& g) {
+    constexpr int D = pick_d(P), G = P / D;
+    float t;
+    const int cx = cell_of(v.x, kp.invh, kp.M, &t);
+    g.ux = centre_offset(t, cx);
+    const int cy = cell_of(v.y, kp.invh, kp.M, &t);
+    const float uy = centre_offset(t, cy);
+    const int cz = cell_of(v.z, kp.invh, kp.M, &t);
+    const float uz = centre_offset(t, cz);
+    fgg<float, P>(uy, kp.beta, kp.E3, g.gy);
+#pragma unroll
+    for (int b = 0; b < P; ++b) g.dgy[b] = (float(b) - 0.5f * float(P - 1) - uy) * g.gy[b];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const float dz = float(k + j * G) - 0.5f * float(P - 1) - uz;
+        g.gz[j] = expf(-kp.beta * dz * dz);
+        g.dgz[j] = dz * g.gz[j];
+    }
+    g.Bx = expf(2.0f * kp.beta * g.ux);
+    g.px0 = expf(-kp.beta * g.ux * (g.ux + float(P - 1)));
+    g.q = v.w;
+    g.base = ((cx - t0x) * Ry + (cy - t0y)) * Rz + (cz - t0z) + k;
+}
+
+template <int P>
+__device__ __forceinline__ void tile_accum(const TilePrep<P>& g, const float* reg, int Ry, int Rz,
+                                           const float* sE3, float& vphi, float& vfx, float& vfy,
+                                           float& vfz) {
+    constexpr int D = pick_d(P), G = P / D;
+    float acc0[D], accx[D], accy[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) acc0[j] = accx[j] = accy[j] = 0.0f;
+    float px = g.px0;
+    const int plane = Ry * Rz;
+#pragma unroll(P <= 8 ? P : 1)
+    for (int a = 0; a < P; ++a) {
+        const float gxa = px * sE3[a];
+        const float dgxa = (float(a) - 0.5f * float(P - 1) - g.ux) * gxa;
+        px *= g.Bx;
+        const float* rowa = reg + g.base + a * plane;
+        float tb0[D], tby[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) tb0[j] = tby[j] = 0.0f;
+#pragma unroll
+        for (int b = 0; b < P; ++b) {
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                const float hv = rowa[b * Rz + j * G];
+                tb0[j] += g.gy[b] * hv;
+                tby[j] += g.dgy[b] * hv;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            acc0[j] += gxa * tb0[j];
+            accx[j] += dgxa * tb0[j];
+            accy[j] += gxa * tby[j];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        vphi += g.gz[j] * acc0[j];
+        vfx += g.gz[j] * accx[j];
+        vfy += g.gz[j] * accy[j];
+        vfz += g.dgz[j] * acc0[j];
+    }
+}
+
+// Copy the grid over a tile region (origin o = tile origin - P/2 + 1, extent
+// Rx x Ry x Rz, wrapped periodically) into shared memory; the whole block.
+__device__ __forceinline__ void load_region(const float* __restrict__ grid, int M, int ox, int oy,
+                                            int oz, int Rx, int Ry, int Rz, float* reg) {
+    const int nel = Rx * Ry * Rz;
+    const FDiv fRz = fdiv_of(Rz), fRy = fdiv_of(Ry);
+    for (int e0 = threadIdx.x; e0 < nel; e0 += blockDim.x * kLoadBatch) {
+        float v[kLoadBatch];
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int e = e0 + u * (int)blockDim.x;
+            if (e < nel) {
+                const int r = fdiv(e, fRz), rz = e - r * Rz;
+                const int rx = fdiv(r, fRy), ry = r - rx * Ry;
+                v[u] = __ldg(grid + ((size_t)wrap_index(ox + rx, M) * M + wrap_index(oy + ry, M)) * M +
+                             wrap_index(oz + rz, M));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int e = e0 + u * (int)blockDim.x;
+            if (e < nel) reg[e] = v[u];
+        }
+    }
+}
+
+// Sum over the G lanes of a particle, then lane 0 of the group writes phi and
+// F at the particle's input position and adds q phi to the energy.
+template <int P>
+__device__ __forceinline__ void gather_emit(int k, bool valid, int orig, float qq, float vphi,
+                                            float vfx, float vfy, float vfz,
+                                            const KParams<float>& kp, float* __restrict__ phi,
+                                            float* __restrict__ F, float phi_mul, float F_mul,
+                                            df2& e_df) {
+    constexpr int G = P / pick_d(P);
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) {
+        const float a0 = __shfl_down_sync(0xffffffffu, vphi, o);
+        const float a1 = __shfl_down_sync(0xffffffffu, vfx, o);
+        const float a2 = __shfl_down_sync(0xffffffffu, vfy, o);
+        const float a3 = __shfl_down_sync(0xffffffffu, vfz, o);
+        if (k + o < G) {
+            vphi += a0;
+            vfx += a1;
+            vfy += a2;
+            vfz += a3;
+        }
+    }
+    if (valid && k == 0) {
+        const float ph = vphi * kp.phi_scale;
+        const float fs = qq * kp.F_scale;
+        if (phi) phi[orig] = ph * phi_mul;
+        if (F) {
+            const float fm = fs * F_mul;
+            F[3 * orig] = fm * vfx;
+            F[3 * orig + 1] = fm * vfy;
+            F[3 * orig + 2] = fm * vfz;
+        }
+        e_df = df_add(e_df, df_from(qq * ph));
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(256, P <= 8 ? 4 : 1)
+k_fgather(const f4* __restrict__ bucket, const int* __restrict__ bucket_idx, int cap,
+          const int* __restrict__ tile_n, const int* __restrict__ over_idx,
+          const f4* __restrict__ wrapped, const float* __restrict__ grid, float* __restrict__ phi,
+          float* __restrict__ F, const KParams<float> kp, double* __restrict__ partials,
+          unsigned* ticket, Acc* acc, double e_scale, double* E_out,
+          const double* __restrict__ adj) {
+    constexpr int D = pick_d(P), G = P / D, GPW = 32 / G;
+    SE_STAMP(6, 0);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* reg = reinterpret_cast<float*>(smem_raw);
+    __shared__ float sE3[P];
+    __shared__ df2 sbuf[32];
+    if (threadIdx.x < P) sE3[threadIdx.x] = kp.E3[threadIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gi = lane / G, k = lane - gi * G;
+    const int group = warp * GPW + gi, ngroups = (blockDim.x >> 5) * GPW;
+    const int tile = blockIdx.x;
+    const int M = kp.M;
+    // the buckets, their counts and the overflow list were written before the
+    // transforms began: the first particle's factors are computed while the
+    // grid is still being produced (before the dependent-launch wait)
+    const int n = tile_n[min(tile, kp.ntiles)];
+    df2 e_df = df_from(0.0f);
+    const float gsc = adj ? (float)__ldg(adj) : 1.0f;
+    const float phi_mul = gsc, F_mul = adj ? -gsc : 1.0f;
+    if (tile < kp.ntiles) {
+        const int nT = kp.nT, TT = kp.tile;
+        const int t0x = (tile / (nT * nT)) * TT, t0y = ((tile / nT) % nT) * TT, t0z = (tile % nT) * TT;
+        const int Rx = min(TT, M - t0x) + P - 1, Ry = min(TT, M - t0y) + P - 1,
+                  Rz = min(TT, M - t0z) + P - 1;
+        TilePrep<P> tp;
+        int orig = -1;
+        if (gi < GPW && group < n) {
+            tile_prep<P>(bucket[(size_t)tile * cap + group], kp, k, t0x, t0y, t0z, Ry, Rz, tp);
+            orig = bucket_idx[(size_t)tile * cap + group];
+        }
+        pdl_wait();
+        SE_STAMP(6, 1);
+        load_region(grid, M, t0x - P / 2 + 1, t0y - P / 2 + 1, t0z - P / 2 + 1, Rx, Ry, Rz, reg);
+        __syncthreads();
+        SE_STAMP(6, 2);
+        for (int p0 = 0; p0 < n; p0 += ngroups) {
+            const int p = p0 + group;
+            const bool valid = gi < GPW && p < n;
+            float vphi = 0.0f, vfx = 0.0f, vfy = 0.0f, vfz = 0.0f;
+            if (valid) {
+                if (p0 != 0) {
+                    tile_prep<P>(bucket[(size_t)tile * cap + p], kp, k, t0x, t0y, t0z, Ry, Rz, tp);
+                    orig = bucket_idx[(size_t)tile * cap + p];
+                }
+                tile_accum<P>(tp, reg, Ry, Rz, sE3, vphi, vfx, vfy, vfz);
+            }
+            gather_emit<P>(k, valid, orig, tp.q, vphi, vfx, vfy, vfz, kp, phi, F, phi_mul, F_mul, e_df);
+        }
+    } else {
+        const int first = (tile - kp.ntiles) * ngroups;   // this CTA's share of the list
+        const int stride = kOverflowBlocks * ngroups;
+        GatherPrep<float, P> gp;
+        float qq = 0.0f;
+        int orig = -1;
+        if (gi < GPW && first + group < n) {
+            orig = over_idx[first + group];
+            const f4 v = wrapped[orig];
+            qq = v.w;
+            gather_prep<float, P>(v, kp, k, gp);
+        }
+        pdl_wait();
+        SE_STAMP(6, 1);
+        for (int o0 = first; o0 < n; o0 += stride) {
+            const int o = o0 + group;
+            const bool valid = gi < GPW && o < n;
+            float vphi = 0.0f, vfx = 0.0f, vfy = 0.0f, vfz = 0.0f;
+            if (valid) {
+                if (o0 != first) {
+                    orig = over_idx[o];
+                    const f4 v = wrapped[orig];
+                    qq = v.w;
+                    gather_prep<float, P>(v, kp, k, gp);
+                }
+                gather_accum<float, P>(gp, grid, kp, sE3, vphi, vfx, vfy, vfz);
+            }
+            gather_emit<P>(k, valid, orig, qq, vphi, vfx, vfy, vfz, kp, phi, F, phi_mul, F_mul, e_df);
+        }
+    }
+    SE_STAMP(6, 3);
+    float* pf = reinterpret_cast<float*>(partials);
+    const df2 r = block_sum_df(e_df, sbuf);
+    SE_STAMP(6, 4);
+    if (threadIdx.x == 0) {
+        pf[2 * blockIdx.x] = r.hi;
+        pf[2 * blockIdx.x + 1] = r.lo;
+    }
+    const bool lastb = last_block(ticket);
+    SE_STAMP(6, 5);
+    if (!lastb || threadIdx.x >= 32) return;
+    const df2 t = warp_sum_partials_df(pf, gridDim.x, 1, 0);
+    SE_STAMP(6, 6);
+    if (threadIdx.x == 0) {
+        const double sum = df_to_double(t);
+        acc->e_gather = sum;
+        if (E_out) *E_out = e_scale * sum;
+        *ticket = 0u;
     }
 }
 

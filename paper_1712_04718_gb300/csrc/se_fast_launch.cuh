@@ -55,7 +55,8 @@ cudaError_t fast_spread_P(const KParams<float>& kp, const FastBufs& b, int nbin,
     const size_t dyn = (P <= 8 && per_sm >= 1 && per_sm <= 5)
                            ? smem_cap_per_sm((size_t)slab * plane, per_sm)
                            : (size_t)slab * plane;
-    return launch_ex(k_fspread<P>, grid, kThreads, dyn, s, true, (const f4*)b.bucket, b.cap, b.tile_count, (const int*)b.over_idx,
+    return launch_ex(k_fspread<P>, grid, kThreads, dyn, s, true, (const f4*)b.bucket, b.cap, b.tile_count,
+                     b.tile_n, (const int*)b.over_idx,
                      (int*)(b.tickets + 4), (const f4*)b.wrapped, (unsigned long long*)b.g64, kp,
                      (const double*)b.partials, nbin, b.tickets + 3, b.acc, slab);
 }
@@ -87,7 +88,7 @@ cudaError_t fast_spread(const float* xyz, const float* q, const KParams<float>& 
     }
     const int nbin = fast_bin_blocks(kp);
     cudaError_t e = launch_ex(k_fbin<float>, nbin, kThreads, 0, s, false, xyz, q, kp, b.tile_count,
-                              (f4*)b.bucket, b.cap, b.over_idx, (int*)(b.tickets + 4),
+                              (f4*)b.bucket, b.bucket_idx, b.cap, b.over_idx, (int*)(b.tickets + 4),
                               (f4*)b.wrapped, b.partials, b.g64);
     if (e != cudaSuccess) return e;
     if (marks) {
@@ -163,6 +164,46 @@ cudaError_t fast_transform(const KParams<float>& kp, const FastBufs& b, double e
     if (e != cudaSuccess) return e;
     if (marks) mark(ctx, 5);
     return cudaSuccess;
+}
+
+template <int P>
+cudaError_t fast_gather_P(const KParams<float>& kp, const FastBufs& b, float* phi, float* F,
+                          double* partials, unsigned* ticket, double e_scale, double* E_out,
+                          const double* adj, cudaStream_t s) {
+    const size_t R = (size_t)kp.tile + P - 1;
+    const size_t bytes = R * R * R * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_fgather<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
+    if (e != cudaSuccess) return e;
+    return launch_ex(k_fgather<P>, kp.ntiles + kOverflowBlocks, kThreads, bytes, s, true,
+                     (const f4*)b.bucket, (const int*)b.bucket_idx, b.cap, (const int*)b.tile_n,
+                     (const int*)b.over_idx, (const f4*)b.wrapped, (const float*)b.rgrid, phi, F,
+                     kp, partials, ticket, b.acc, e_scale, E_out, adj);
+}
+
+// The tile gather pays when a tile's particles read many more grid values
+// than its region holds (mean particles per tile x P^3 >= 8 x region): the
+// region is then loaded once instead of every particle reading L2.  It needs
+// the region within kTileGatherSmem and a CTA count within the energy
+// partials' space.
+bool fast_gather_tiled(const KParams<float>& kp) {
+    const double R = (double)kp.tile + kp.P - 1;
+    const double per_tile = (double)kp.N / kp.ntiles;
+    return R * R * R * sizeof(float) <= (double)kTileGatherSmem &&
+           kp.ntiles + kOverflowBlocks <= 4 * kMaxPartials &&
+           per_tile * kp.P * kp.P * kp.P >= 8.0 * R * R * R;
+}
+
+cudaError_t fast_gather(const KParams<float>& kp, const FastBufs& b, float* phi, float* F,
+                        double* partials, unsigned* ticket, double e_scale, double* E_out,
+                        const double* adj, cudaStream_t s) {
+    switch (kp.P) {
+#define SE_CASE(PP) \
+    case PP: return fast_gather_P<PP>(kp, b, phi, F, partials, ticket, e_scale, E_out, adj, s);
+        SE_FOR_EACH_P(SE_CASE)
+#undef SE_CASE
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t fast_to_real(const FastBufs& b, int M, float* dst, cudaStream_t s) {

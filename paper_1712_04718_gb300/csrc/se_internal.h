@@ -85,6 +85,8 @@ struct FastBufs {
     const float* green_f; // the same table rounded to float
     int* tile_count;
     void* bucket;         // f4 [ntiles * cap]: particles by tile
+    int* bucket_idx;      // [ntiles * cap]: their input positions
+    int* tile_n;          // [ntiles + 1]: particles in each bucket, then the overflow count
     int cap;              // bucket capacity
     int* over_idx;        // [N] particles that found their bucket full
     void* wrapped;        // f4 [N]: wrapped (x, y, z, q) in input order, for the gather
@@ -98,6 +100,10 @@ struct FastBufs {
 cudaError_t fast_spread(const float* xyz, const float* q, const KParams<float>& kp,
                         const FastBufs& b, cudaStream_t s, bool marks, void (*mark)(void*, int),
                         void* ctx);
+bool fast_gather_tiled(const KParams<float>& kp);
+cudaError_t fast_gather(const KParams<float>& kp, const FastBufs& b, float* phi, float* F,
+                        double* partials, unsigned* ticket, double e_scale, double* E_out,
+                        const double* adj, cudaStream_t s);
 cudaError_t fast_transform(const KParams<float>& kp, const FastBufs& b, double e_scale,
                            double* E_grid, cudaStream_t s, bool marks, void (*mark)(void*, int),
                            void* ctx);
@@ -112,5 +118,6 @@ constexpr int kFastMaxM = 128;       // largest grid of the single-precision pip
 constexpr int kScanLimit = 8192;     // tiles scanned in shared memory
 constexpr size_t kSmemBudget = 200 * 1024;  // dynamic shared memory for a spreading tile
 constexpr size_t kSlabSmemFloor = 116 * 1024;  // > half of an SM's 228 KB: one slab CTA per SM
+constexpr size_t kTileGatherSmem = 48 * 1024;  // largest tile region staged by the tile gather
 
 }  // namespace se

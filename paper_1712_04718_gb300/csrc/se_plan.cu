@@ -62,6 +62,7 @@ struct se_plan {
     int* perm = nullptr;
     void* sorted = nullptr;
     void* bucket = nullptr;        // tile buckets (single-precision pipeline)
+    int* bucket_idx = nullptr;     // their input positions
     long long* g64 = nullptr;      // fixed-point spread grid (single-precision pipeline)
     float* green_f = nullptr;      // G(k) table in float (single-precision pipeline)
     void* tw = nullptr;            // twiddles of the single-precision pipeline
@@ -198,10 +199,11 @@ void release_device(se_plan* p) {
     void* bufs[] = {p->grid_spread, p->grid_gather, p->cgrid, p->green, p->tile_count,
                     p->tile_start, p->slot, p->tile_of, p->perm, p->sorted, p->partials,
                     p->tickets, p->acc, p->dE, p->h_xyz, p->h_q, p->h_F, p->h_phi, p->g64, p->tw, p->green_f,
-                    p->bucket};
+                    p->bucket, p->bucket_idx};
     for (void* b : bufs)
         if (b) cudaFree(b);
     p->grid_spread = p->grid_gather = p->cgrid = p->sorted = p->tw = p->bucket = nullptr;
+    p->bucket_idx = nullptr;
     p->g64 = nullptr;
     p->green_f = nullptr;
     p->green = p->partials = p->dE = nullptr;
@@ -284,6 +286,8 @@ int prepare(se_plan* p) {
     if (rc == SE_OK && fast) rc = dalloc((void**)&p->g64, M3 * sizeof(long long));
     if (rc == SE_OK && p->variant == 3)
         rc = dalloc(&p->bucket, (size_t)p->ntiles * p->cap * 4 * sizeof(float));
+    if (rc == SE_OK && p->variant == 3)
+        rc = dalloc((void**)&p->bucket_idx, (size_t)p->ntiles * p->cap * sizeof(int));
     if (rc == SE_OK && fast) rc = dalloc(&p->tw, (size_t)p->M * 2 * sizeof(float));
     if (rc == SE_OK && fast) rc = dalloc((void**)&p->green_f, nc * sizeof(float));
     if (rc == SE_OK) rc = dalloc(&p->grid_gather, M3 * ts);
@@ -376,6 +380,8 @@ se::FastBufs fast_bufs(se_plan* p) {
     b.green_f = p->green_f;
     b.tile_count = p->tile_count;
     b.bucket = p->bucket;
+    b.bucket_idx = p->bucket_idx;
+    b.tile_n = p->tile_start;
     b.cap = p->cap;
     b.over_idx = p->slot;
     b.wrapped = p->sorted;
@@ -417,6 +423,13 @@ int fast_scale(se_plan* p, double* E_grid) {
 
 int fast_gather(se_plan* p, void* phi, void* F, double* E, const double* adj = nullptr) {
     const KParams<float> kp = make_kparams<float>(p);
+    if (p->variant == 3 && se::fast_gather_tiled(kp)) {
+        SE_CUDA(se::fast_gather(kp, fast_bufs(p), (float*)phi, (float*)F,
+                                p->partials + 4 * se::kMaxPartials, p->tickets + 2, 0.5, E, adj,
+                                p->stream));
+        timing_mark(p, 6);
+        return SE_OK;
+    }
     SE_CUDA(se::launch_gather_pdl((const se::f4*)p->sorted, nullptr, (const float*)p->grid_gather,
                                   (float*)phi, (float*)F, kp, p->partials + 4 * se::kMaxPartials,
                                   p->tickets + 2, p->acc, 0.5, E, adj, p->stream));

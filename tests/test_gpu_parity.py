@@ -445,3 +445,37 @@ def test_crowded_tile_overflow(variant):
         assert rel(phi.double().cpu().numpy(), r["phi"]) < 5 * TOL["fp32"]
         assert abs(E - r["E"]) < 5 * TOL["fp32"] * abs(r["E"])
     plan.close()
+
+
+def test_tile_gather_dense_tiles():
+    """Dense tiles (about 55 particles per 6^3-cell tile at P = 6) select the
+    gather that stages each tile's grid region in shared memory: elementwise
+    against the oracle, and equal to the per-particle gather of a plan whose
+    tiles are too sparse for it (same arithmetic, same order)."""
+    L, xi, M, P = 2.0, 4.0, 32, 6
+    N = 12000
+    x, q = systems.uniform_charges(N, L, seed=61, dtype=np.float32)
+    r = oracle_for(x, q, L, xi, M, P, "fp32")
+    g = run_gpu(x, q, L, xi, M, P, "fp32", spread_variant=3, tile=6)
+    assert rel(g["F"], r["F"]) < 5 * TOL["fp32"]
+    assert rel(g["phi"], r["phi"]) < 5 * TOL["fp32"]
+    assert abs(g["E"] - r["E"]) < 5 * TOL["fp32"] * abs(r["E"])
+    g4 = run_gpu(x, q, L, xi, M, P, "fp32", spread_variant=3, tile=4)   # sparse tiles
+    assert rel(g["F"], g4["F"]) < 1e-6 and rel(g["phi"], g4["phi"]) < 1e-6
+
+
+def test_tile_gather_with_overflow():
+    """Dense tiles with one crowded tile (4000 of 6000 charges): the tile
+    gather and its overflow CTAs, against the oracle, twice in a row."""
+    L, xi, M, P = 2.0, 4.0, 24, 4
+    rng = np.random.default_rng(62)
+    x, q = systems.uniform_charges(6000, L, seed=63, dtype=np.float32)
+    x[:4000] = (0.71 + 0.12 * rng.random((4000, 3))).astype(np.float32)
+    plan = se.Plan(6000, L, xi, M, P, precision="fp32", spread_variant=3, tile=8)
+    r = oracle_for(x, q, L, xi, M, P, "fp32")
+    for _ in range(2):
+        E, F, phi = plan.energy_force(torch.tensor(x, device="cuda"), torch.tensor(q, device="cuda"))
+        assert rel(F.double().cpu().numpy(), r["F"]) < 5 * TOL["fp32"]
+        assert rel(phi.double().cpu().numpy(), r["phi"]) < 5 * TOL["fp32"]
+        assert abs(E - r["E"]) < 5 * TOL["fp32"] * abs(r["E"])
+    plan.close()
