@@ -269,15 +269,84 @@ k_bgather(const f4* __restrict__ sorted, const int* __restrict__ perm, const flo
     }
 }
 
+// Gather by tiles of every system, for dense tiles: CTA t stages the real
+// grid over global tile t's region of its system in shared memory, gathers
+// the tile's particles (tile order) from it and leaves the tile's energy
+// partial 1/2 sum q phi (a double-float pair) in e_tile[t].
+template <int P>
+__global__ void __launch_bounds__(256, P <= 8 ? 4 : 1)
+k_bgather_tile(const f4* __restrict__ sorted, const int* __restrict__ perm,
+               const int* __restrict__ tile_start, const float* __restrict__ R,
+               const SysParams* __restrict__ sys, const int* __restrict__ tile_sys,
+               float* __restrict__ phi, float* __restrict__ F, float* __restrict__ e_tile) {
+    constexpr int D = pick_d(P), G = P / D, GPW = 32 / G;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* reg = reinterpret_cast<float*>(smem_raw);
+    __shared__ df2 sbuf[32];
+    __shared__ float sE3[P];
+    const int s = tile_sys[blockIdx.x];
+    const SysParams& sp = sys[s];
+    const KParams<float>& kp = sp.kp;
+    const int tile = blockIdx.x - sp.t0;
+    if (threadIdx.x < P) sE3[threadIdx.x] = kp.E3[threadIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gi = lane / G, k = lane - gi * G;
+    const int group = warp * GPW + gi, ngroups = (blockDim.x >> 5) * GPW;
+    const int M = kp.M, nT = kp.nT, TT = kp.tile;
+    const int t0x = (tile / (nT * nT)) * TT, t0y = ((tile / nT) % nT) * TT, t0z = (tile % nT) * TT;
+    const int Rx = min(TT, M - t0x) + P - 1, Ry = min(TT, M - t0y) + P - 1,
+              Rz = min(TT, M - t0z) + P - 1;
+    pdl_wait();
+    pdl_launch_next();
+    const int pb = tile_start[blockIdx.x], n = tile_start[blockIdx.x + 1] - pb;
+    TilePrep<P> tp;
+    int orig = -1;
+    if (gi < GPW && group < n) {
+        tile_prep<P>(sorted[pb + group], kp, k, t0x, t0y, t0z, Ry, Rz, tp);
+        orig = perm[pb + group];
+    }
+    load_region(R + sp.g0, M, t0x - P / 2 + 1, t0y - P / 2 + 1, t0z - P / 2 + 1, Rx, Ry, Rz, reg);
+    __syncthreads();
+    df2 e_df = df_from(0.0f);
+    for (int p0 = 0; p0 < n; p0 += ngroups) {
+        const int p = p0 + group;
+        const bool valid = gi < GPW && p < n;
+        float vphi = 0.0f, vfx = 0.0f, vfy = 0.0f, vfz = 0.0f;
+        if (valid) {
+            if (p0 != 0) {
+                tile_prep<P>(sorted[pb + p], kp, k, t0x, t0y, t0z, Ry, Rz, tp);
+                orig = perm[pb + p];
+            }
+            tile_accum<P>(tp, reg, Ry, Rz, sE3, vphi, vfx, vfy, vfz);
+        }
+        gather_emit<P>(k, valid, orig, tp.q, vphi, vfx, vfy, vfz, kp, phi, F, 1.0f, 1.0f, e_df);
+    }
+    const df2 r = block_sum_df(e_df, sbuf);
+    if (threadIdx.x == 0) {
+        e_tile[2 * blockIdx.x] = 0.5f * r.hi;    // exact: a power-of-two scale
+        e_tile[2 * blockIdx.x + 1] = 0.5f * r.lo;
+    }
+}
+
 __global__ void __launch_bounds__(256)
-k_bfinish(const float* __restrict__ e_part, const float* __restrict__ x_part,
-          const SysParams* __restrict__ sys, double* __restrict__ E, double* __restrict__ Eg) {
+k_bfinish(const float* __restrict__ e_part, const float* __restrict__ e_tile, int tiled,
+          const float* __restrict__ x_part, const SysParams* __restrict__ sys,
+          double* __restrict__ E, double* __restrict__ Eg) {
     pdl_wait();
     __shared__ df2 sbuf[32];
     const int s = blockIdx.x;
     const SysParams& sp = sys[s];
     df2 a = df_from(0.0f), b = df_from(0.0f);
-    for (int i = threadIdx.x; i < sp.kp.N; i += blockDim.x) a = df_add(a, df_from(e_part[sp.p0 + i]));
+    if (tiled) {   // one double-float partial per tile of the system
+        for (int i = threadIdx.x; i < sp.kp.ntiles; i += blockDim.x) {
+            df2 u;
+            u.hi = e_tile[2 * (sp.t0 + i)];
+            u.lo = e_tile[2 * (sp.t0 + i) + 1];
+            a = df_add(a, u);
+        }
+    } else {
+        for (int i = threadIdx.x; i < sp.kp.N; i += blockDim.x) a = df_add(a, df_from(e_part[sp.p0 + i]));
+    }
     for (int i = threadIdx.x; i < sp.nx; i += blockDim.x) {
         df2 u;
         u.hi = x_part[2 * (sp.x0 + i)];
@@ -322,6 +391,7 @@ struct se_batch {
     float* green = nullptr;
     float2* tw = nullptr;
     float* e_part = nullptr;
+    float* e_tile = nullptr;   // per-tile energy partials of the tile gather
     float* x_part = nullptr;
     double* Eg = nullptr;
     int alloc_tiles = 0;   // capacity of the tile arrays
@@ -341,7 +411,7 @@ void free_all(se_batch* b) {
     b->gexec = nullptr;
     void* p[] = {b->d_sys, b->d_bacc, b->tile_count, b->tile_start, b->slot, b->tile_of, b->perm,
                  b->tile_sys, b->slab_sys, b->x_sys, b->sorted, b->g64, b->cgrid, b->rgrid,
-                 b->green, b->tw, b->e_part, b->x_part, b->Eg};
+                 b->green, b->tw, b->e_part, b->x_part, b->Eg, b->e_tile};
     for (void* x : p)
         if (x) cudaFree(x);
     b->d_sys = nullptr;
@@ -351,7 +421,7 @@ void free_all(se_batch* b) {
     b->sorted = nullptr;
     b->g64 = nullptr;
     b->cgrid = nullptr;
-    b->rgrid = b->green = b->e_part = b->x_part = nullptr;
+    b->rgrid = b->green = b->e_part = b->x_part = b->e_tile = nullptr;
     b->tw = nullptr;
     b->Eg = nullptr;
     b->alloc_tiles = 0;
@@ -425,11 +495,14 @@ int build_tables(se_batch* b) {
         if (b->tile_count) cudaFree(b->tile_count);
         if (b->tile_start) cudaFree(b->tile_start);
         if (b->tile_sys) cudaFree(b->tile_sys);
+        if (b->e_tile) cudaFree(b->e_tile);
         b->tile_count = b->tile_start = b->tile_sys = nullptr;
+        b->e_tile = nullptr;
         int rc = SE_OK;
         if (rc == SE_OK) rc = balloc(&b->tile_count, b->Ttot);
         if (rc == SE_OK) rc = balloc(&b->tile_start, b->Ttot + 1);
         if (rc == SE_OK) rc = balloc(&b->tile_sys, b->Ttot);
+        if (rc == SE_OK) rc = balloc(&b->e_tile, 2 * (size_t)b->Ttot);
         if (rc != SE_OK) return rc;
         b->alloc_tiles = b->Ttot;
     }
@@ -559,6 +632,28 @@ cudaError_t launch_bgather(se_batch* b, float* phi, float* F, cudaStream_t s) {
                          b->Ntot, phi, F, b->e_part);
 }
 
+template <int P>
+cudaError_t launch_bgather_tile(se_batch* b, float* phi, float* F, cudaStream_t s) {
+    const size_t R = (size_t)b->tile + P - 1;
+    const size_t bytes = R * R * R * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(se::k_bgather_tile<P>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    return se::launch_ex(se::k_bgather_tile<P>, b->Ttot, se::kThreads, bytes, s, true,
+                         (const se::f4*)b->sorted, (const int*)b->perm, (const int*)b->tile_start,
+                         (const float*)b->rgrid, (const SysParams*)b->d_sys,
+                         (const int*)b->tile_sys, phi, F, b->e_tile);
+}
+
+// The tile gather for dense tiles (mean particles per tile x P^3 at least 8
+// times the region) whose region fits the shared-memory budget.
+bool batch_gather_tiled(const se_batch* b) {
+    const double R = (double)b->tile + b->P - 1;
+    const double per_tile = (double)b->Ntot / std::max(1, b->Ttot);
+    return R * R * R * sizeof(float) <= (double)se::kTileGatherSmem &&
+           per_tile * b->P * b->P * b->P >= 8.0 * R * R * R;
+}
+
 int batch_launch(se_batch* b, const float* xyz, const float* q, float* F, float* phi, double* E,
                  cudaStream_t s) {
     cudaError_t e;
@@ -593,15 +688,18 @@ int batch_launch(se_batch* b, const float* xyz, const float* q, float* F, float*
                       b->rgrid, (const float2*)b->tw, (const SysParams*)b->d_sys,
                       (const int*)b->slab_sys);
     if (e != cudaSuccess) return SE_ERR_CUDA;
+    const bool tiled = batch_gather_tiled(b);
     switch (b->P) {
-#define SE_CASE(PP) case PP: e = launch_bgather<PP>(b, phi, F, s); break;
+#define SE_CASE(PP) \
+    case PP: e = tiled ? launch_bgather_tile<PP>(b, phi, F, s) : launch_bgather<PP>(b, phi, F, s); break;
         SE_FOR_EACH_P(SE_CASE)
 #undef SE_CASE
         default: return SE_ERR_UNSUPPORTED;
     }
     if (e != cudaSuccess) return SE_ERR_CUDA;
     e = se::launch_ex(se::k_bfinish, b->S, se::kThreads, 0, s, true, (const float*)b->e_part,
-                      (const float*)b->x_part, (const SysParams*)b->d_sys, E, b->Eg);
+                      (const float*)b->e_tile, (int)tiled, (const float*)b->x_part,
+                      (const SysParams*)b->d_sys, E, b->Eg);
     return e == cudaSuccess ? SE_OK : SE_ERR_CUDA;
 }
 
