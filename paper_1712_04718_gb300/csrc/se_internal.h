@@ -118,6 +118,6 @@ constexpr int kFastMaxM = 128;       // largest grid of the single-precision pip
 constexpr int kScanLimit = 8192;     // tiles scanned in shared memory
 constexpr size_t kSmemBudget = 200 * 1024;  // dynamic shared memory for a spreading tile
 constexpr size_t kSlabSmemFloor = 116 * 1024;  // > half of an SM's 228 KB: one slab CTA per SM
-constexpr size_t kTileGatherSmem = 48 * 1024;  // largest tile region staged by the tile gather
+constexpr size_t kTileGatherSmem = 64 * 1024;  // largest tile region staged by the tile gather
 
 }  // namespace se

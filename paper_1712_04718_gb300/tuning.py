@@ -95,7 +95,7 @@ def tune_plan(plan, xyz, q, configs=None, reps=50, use_cache=True):
     return best[0], best[1], best[2], False
 
 
-def tune_batch(batch, xyz, q, candidates=(4, 6, 8, 10), reps=10, use_cache=True):
+def tune_batch(batch, xyz, q, candidates=(6, 8, 10, 12, 16), reps=10, use_cache=True):
     """Pick the tile edge of an ensemble (se_batch_autotune); returns (tile, ms, cached)."""
     key = "batch:P%d:S%d:M%d-%d:N%dk:%s" % (batch.P, batch.S, int(batch.Ms.min()),
                                              int(batch.Ms.max()), batch.Ntot // 1000, _gpu())
