@@ -306,16 +306,35 @@ __device__ __forceinline__ void spread_tile(const f4* __restrict__ parts, int n,
                 const float Bx = expf(2.0f * kp.beta * ux);
                 float px = expf(-kp.beta * ux * (ux + float(P - 1)) + 2.0f * kp.beta * ux * float(alo));
                 unsigned* row = acc + ((lx + alo - s0) * Ry + ly) * Rz + lz + k;
+                // small supports: the z factors folded into the y factors
+                // (one multiply per weight); a running row pointer keeps the
+                // address of each atomic to one add
+                constexpr bool kFold = P * D <= 16;
+                float gyz[kFold ? P * D : 1];
+                if constexpr (kFold) {
+#pragma unroll
+                    for (int b = 0; b < P; ++b)
+#pragma unroll
+                        for (int j = 0; j < D; ++j) gyz[b * D + j] = gy[b] * gz[j];
+                }
 #pragma unroll 1
                 for (int a = alo; a < ahi; ++a) {
                     const float gxa = px * sE3[a];
                     px *= Bx;
+                    unsigned* rb = row;
 #pragma unroll
                     for (int b = 0; b < P; ++b) {
-                        const float wab = gxa * gy[b];
+                        if constexpr (kFold) {
 #pragma unroll
-                        for (int j = 0; j < D; ++j)
-                            atomicAdd(row + b * Rz + j * G, (unsigned)__float2int_rn(wab * gz[j]));
+                            for (int j = 0; j < D; ++j)
+                                atomicAdd(rb + j * G, (unsigned)__float2int_rn(gxa * gyz[b * D + j]));
+                        } else {
+                            const float wab = gxa * gy[b];
+#pragma unroll
+                            for (int j = 0; j < D; ++j)
+                                atomicAdd(rb + j * G, (unsigned)__float2int_rn(wab * gz[j]));
+                        }
+                        rb += Rz;
                     }
                     row += plane;
                 }
@@ -567,7 +586,7 @@ __device__ __forceinline__ void tile_accum(const TilePrep<P>& g, const float* re
         const float gxa = px * sE3[a];
         const float dgxa = (float(a) - 0.5f * float(P - 1) - g.ux) * gxa;
         px *= g.Bx;
-        const float* rowa = reg + g.base + a * plane;
+        const float* rb = reg + g.base + a * plane;   // running row pointer: one add per row
         float tb0[D], tby[D];
 #pragma unroll
         for (int j = 0; j < D; ++j) tb0[j] = tby[j] = 0.0f;
@@ -575,10 +594,11 @@ __device__ __forceinline__ void tile_accum(const TilePrep<P>& g, const float* re
         for (int b = 0; b < P; ++b) {
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                const float hv = rowa[b * Rz + j * G];
+                const float hv = rb[j * G];
                 tb0[j] += g.gy[b] * hv;
                 tby[j] += g.dgy[b] * hv;
             }
+            rb += Rz;
         }
 #pragma unroll
         for (int j = 0; j < D; ++j) {
