@@ -61,6 +61,35 @@ def dist_env():
     return ws, rank, local
 
 
+def system_cost(N, M, P):
+    """Work of one system's evaluation: N P^3 for spread and gather, plus
+    M^3 log2 M for the transforms."""
+    return float(N) * P ** 3 + float(M) ** 3 * math.log2(max(M, 2))
+
+
+def partition_systems(costs, ws):
+    """Systems -> ranks, balanced by cost (largest first onto the least loaded
+    rank; ties to the lower rank): every rank computes the same assignment, so
+    no exchange is needed.  Returns the sorted system indices of each rank."""
+    load = [0.0] * ws
+    parts = [[] for _ in range(ws)]
+    for i in sorted(range(len(costs)), key=lambda i: (-costs[i], i)):
+        r = min(range(ws), key=lambda r: (load[r], r))
+        parts[r].append(i)
+        load[r] += costs[i]
+    return [sorted(p) for p in parts]
+
+
+def max_over_ranks(value, ws, device):
+    """The largest value over all ranks (the slowest rank's time)."""
+    if ws <= 1:
+        return value
+    import torch
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.item()
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clock and throttle reasons while running."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -303,10 +332,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     plan.set_timing(False)
     stages, nstage = plan.get_timing(reset=True)
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = t.item()
+    total_ms = max_over_ranks(total_ms, ws, "cuda")
     ms_step = total_ms / K
     value = ws * K / (total_ms / 1e3)
 
@@ -383,13 +409,14 @@ def run_ours(args):
 
 def run_ensemble(args, torch, se, ws, rank):
     """The batched ensemble: every rank evaluates its share of the systems
-    (round robin) through one se_batch; value = evaluations of the whole
+    (balanced by cost, partition_systems) through one se_batch; value = evaluations of the whole
     ensemble per second of the slowest rank (strong scaling: the ensemble is
     fixed)."""
     from paper_1712_04718_gb300 import systems, tuning
     w = systems.WORKLOADS[args.workload]
     ens = systems.ensemble(S=w["S"], spacing=w["spacing"])
-    mine = ens[rank::ws]
+    parts = partition_systems([system_cost(len(d["q"]), d["M"], w["P"]) for d in ens], ws)
+    mine = [ens[i] for i in parts[rank]]
     Ns = [len(d["q"]) for d in mine]
     b = se.Batch(Ns, [d["L"] for d in mine], [d["M"] for d in mine], w["xi"], w["P"])
     xd = torch.tensor(np.concatenate([d["x"] for d in mine]), device="cuda")
@@ -429,10 +456,7 @@ def run_ensemble(args, torch, se, ws, rank):
         torch.distributed.barrier()
     clk = clocks.stop()
     total_ms = sum(a.elapsed_time(c) for a, c in zip(st, en))
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = t.item()
+    total_ms = max_over_ranks(total_ms, ws, "cuda")
     ms_step = total_ms / K
     Nall = sum(len(d["q"]) for d in ens)
     out = {
