@@ -175,9 +175,9 @@ int se_energy_force_host(se_plan *plan, const void *xyz, const void *q,
 
 /* Copy one of the plan's grids into dst (device, M^3 values of the plan's
  * type, z fastest): which = 0 spread grid H (after se_spread), 1 scaled and
- * back-transformed grid Ht (after se_scale).  With spread variant 4 the
- * spread grid is cleared by se_scale: which = 0 after se_scale returns
- * SE_ERR_ARG.  For tests and inspection. */
+ * back-transformed grid Ht (after se_scale).  With the single-precision
+ * pipeline (spread variants 3 and 4) the spread grid is cleared by se_scale:
+ * which = 0 after se_scale returns SE_ERR_ARG.  For tests and inspection. */
 int se_copy_grid(se_plan *plan, int which, void *dst);
 
 /* Self-energy term of Eq. 1.6, -kc xi / sqrt(pi) sum q^2, from HOST charges

@@ -3,7 +3,7 @@
 //
 //   k_fbin      tile of each particle and a slot in the tile's bucket (a
 //               fixed-capacity list; full buckets spill to an overflow list),
-//               q sums and max |q|; clears the fixed-point spread grid
+//               q sums and max |q|
 //   k_fspread   Eq. 3.5, one CTA per tile: 32-bit fixed-point sums in shared
 //               memory at a per-tile scale (one native 32-bit atomic per
 //               weight), flushed exactly into the 64-bit fixed-point grid with
@@ -11,7 +11,8 @@
 //               of the additions; a few more CTAs add the overflow list with
 //               global 64-bit atomics
 //   k_slab_fwd  per x-slab: forward DFT along z (real to complex; the
-//               fixed-point grid is converted to float here), then along y;
+//               fixed-point grid is converted to float here and cleared for
+//               the next evaluation), then along y;
 //               k_slab_fwd_cl the same on a 2-CTA cluster per slab
 //   k_xpass     forward DFT along x, scaling by G(k)/M^3 (Eq. 3.6) with the
 //               grid energy partials, inverse DFT along x
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(256)
 k_fbin(const T* __restrict__ xyz, const T* __restrict__ q, const KParams<T> kp,
        int* __restrict__ tile_count, v4_t<T>* __restrict__ bucket, int* __restrict__ bucket_idx,
        int cap, int* __restrict__ over_idx, int* __restrict__ n_over, v4_t<T>* __restrict__ wrapped,
-       double* __restrict__ partials, long long* __restrict__ g64) {
+       double* __restrict__ partials) {
     SE_STAMP(0, 0);
     pdl_wait();
     pdl_launch_next();
@@ -100,10 +101,6 @@ k_fbin(const T* __restrict__ xyz, const T* __restrict__ q, const KParams<T> kp,
     __shared__ df2 sbuf[32];
     __shared__ int sbad;
     if (threadIdx.x == 0) sbad = 0;
-    const long long M3 = (long long)kp.M * kp.M * kp.M;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < M3; i += stride)
-        g64[i] = 0;
     SE_STAMP(0, 2);
     df2 sq = df_from(0.0f), sa = df_from(0.0f);
     float qmax = 0.0f;
@@ -936,7 +933,7 @@ __host__ __device__ inline size_t slab_smem_bytes(int M) {
 // Forward 2-D transform (z real-to-complex, then y) of x-slab x.  The input
 // is the fixed-point grid (long long, scaled by inv), or the float grid of
 // the unsorted spread (float), which is cleared after it is read.
-template <typename G>
+template <typename G, bool kClear = (sizeof(G) == sizeof(float))>
 __device__ __forceinline__ void slab_fwd_body(G* __restrict__ grid, float2* __restrict__ C,
                                               const float2* __restrict__ tw_g, int M, float inv,
                                               int x, unsigned char* sm) {
@@ -970,6 +967,7 @@ __device__ __forceinline__ void slab_fwd_body(G* __restrict__ grid, float2* __re
                 const unsigned long long w = (unsigned long long)v[u];
                 const float hi = (float)(int)(w >> 32), lo = (float)(unsigned)(w & 0xffffffffull);
                 S[y * SP + z] = fmaf(hi, 4294967296.0f, lo) * inv;
+                if constexpr (kClear) src[e] = 0;
             }
         }
     }
@@ -986,14 +984,14 @@ __device__ __forceinline__ void slab_fwd_body(G* __restrict__ grid, float2* __re
 
 #ifndef SE_BATCH_TU
 __global__ void __launch_bounds__(kSlabThreads)
-k_slab_fwd(const long long* __restrict__ g64, float2* __restrict__ C,
+k_slab_fwd(long long* __restrict__ g64, float2* __restrict__ C,
            const float2* __restrict__ tw_g, int M, const Acc* __restrict__ acc) {
     SE_STAMP(3, 0);
     pdl_wait();
     pdl_launch_next();
     SE_STAMP(3, 1);
     extern __shared__ __align__(16) unsigned char sm[];
-    slab_fwd_body(g64, C, tw_g, M, acc->fx_inv, blockIdx.x, sm);
+    slab_fwd_body<long long, true>(g64, C, tw_g, M, acc->fx_inv, blockIdx.x, sm);   // clears the grid
 }
 
 // the same on the float grid of the unsorted spread (cleared after reading)
@@ -1212,7 +1210,7 @@ __host__ __device__ inline SlabClLayout slabcl_layout(int M) {
 
 #ifndef SE_BATCH_TU
 __global__ void __launch_bounds__(kSlabThreads)
-k_slab_fwd_cl(const long long* __restrict__ g64, float2* __restrict__ Cg,
+k_slab_fwd_cl(long long* __restrict__ g64, float2* __restrict__ Cg,
               const float2* __restrict__ tw_g, int M, const Acc* __restrict__ acc) {
     namespace cg = cooperative_groups;
     SE_STAMP(3, 0);
@@ -1234,7 +1232,7 @@ k_slab_fwd_cl(const long long* __restrict__ g64, float2* __restrict__ Cg,
     load_twiddles(tw, tw_g, M);
     const float inv = acc->fx_inv;
     const FDiv fM = fdiv_of(M);
-    const long long* src = g64 + ((size_t)x * M + y0) * M;
+    long long* src = g64 + ((size_t)x * M + y0) * M;   // read, then cleared for the next evaluation
     for (int e0 = threadIdx.x; e0 < ny * M; e0 += blockDim.x * kLoadBatch) {
         long long v[kLoadBatch];
 #pragma unroll
@@ -1250,6 +1248,7 @@ k_slab_fwd_cl(const long long* __restrict__ g64, float2* __restrict__ Cg,
             const unsigned long long w = (unsigned long long)v[u];
             const float hi = (float)(int)(w >> 32), lo = (float)(unsigned)(w & 0xffffffffull);
             S[yl * SP + z] = fmaf(hi, 4294967296.0f, lo) * inv;
+            src[e] = 0;
         }
     }
     __syncthreads();

@@ -11,8 +11,7 @@
 namespace se {
 
 inline int fast_bin_blocks(const KParams<float>& kp) {
-    const long long m3 = (long long)kp.M * kp.M * kp.M;
-    long long b = std::max<long long>((kp.N + 255) / 256, (m3 + 2047) / 2048);
+    const long long b = ((long long)kp.N + 255) / 256;
     return (int)std::max<long long>(1, std::min<long long>(b, kMaxPartials));
 }
 
@@ -89,7 +88,7 @@ cudaError_t fast_spread(const float* xyz, const float* q, const KParams<float>& 
     const int nbin = fast_bin_blocks(kp);
     cudaError_t e = launch_ex(k_fbin<float>, nbin, kThreads, 0, s, false, xyz, q, kp, b.tile_count,
                               (f4*)b.bucket, b.bucket_idx, b.cap, b.over_idx, (int*)(b.tickets + 4),
-                              (f4*)b.wrapped, b.partials, b.g64);
+                              (f4*)b.wrapped, b.partials);
     if (e != cudaSuccess) return e;
     if (marks) {
         mark(ctx, 0);
@@ -127,8 +126,8 @@ cudaError_t fast_transform(const KParams<float>& kp, const FastBufs& b, double e
         } else {
             e = cudaFuncSetAttribute(k_slab_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab);
             if (e != cudaSuccess) return e;
-            e = launch_ex(k_slab_fwd, M, kSlabThreads, slab, s, true, (const long long*)b.g64, C, tw,
-                          M, (const Acc*)b.acc);
+            e = launch_ex(k_slab_fwd, M, kSlabThreads, slab, s, true, b.g64, C, tw, M,
+                          (const Acc*)b.acc);
         }
     } else {
         // 2-CTA clusters per x-slab, at most ceil(2M / SMs) CTAs per SM
@@ -137,7 +136,7 @@ cudaError_t fast_transform(const KParams<float>& kp, const FastBufs& b, double e
         e = cudaFuncSetAttribute(k_slab_fwd_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cl);
         if (e != cudaSuccess) return e;
         e = launch_cluster(k_slab_fwd_cl, kSlabCL * M, kSlabThreads, cl, kSlabCL, s, true,
-                           (const long long*)b.g64, C, tw, M, (const Acc*)b.acc);
+                           b.g64, C, tw, M, (const Acc*)b.acc);
     }
     if (e != cudaSuccess) return e;
     if (marks) mark(ctx, 3);

@@ -313,7 +313,7 @@ int prepare(se_plan* p) {
         cudaMemset(p->tickets, 0, 8 * sizeof(unsigned)) != cudaSuccess ||
         cudaMemset(p->acc, 0, sizeof(Acc)) != cudaSuccess ||
         (!fast && cudaMemset(p->grid_spread, 0, M3 * ts) != cudaSuccess) ||
-        (p->variant == 4 && cudaMemset(p->g64, 0, M3 * sizeof(float)) != cudaSuccess)) {
+        (p->variant >= 3 && cudaMemset(p->g64, 0, M3 * sizeof(long long)) != cudaSuccess)) {
         release_device(p);
         return SE_ERR_CUDA;
     }
@@ -397,14 +397,15 @@ void mark_cb(void* ctx, int s) { timing_mark(static_cast<se_plan*>(ctx), s); }
 
 int fast_spread(se_plan* p, const void* xyz, const void* q) {
     const KParams<float> kp = make_kparams<float>(p);
-    // the unsorted spread adds into the float grid, which k_slab_fwd_f clears
-    if (p->variant == 4 && !p->spread_clean)
-        SE_CUDA(cudaMemsetAsync(p->g64, 0, (size_t)p->M * p->M * p->M * sizeof(float), p->stream));
+    // the spread adds into g64 (fixed point, or float with variant 4), which
+    // the forward slab kernel clears as it reads it
+    if (!p->spread_clean)
+        SE_CUDA(cudaMemsetAsync(p->g64, 0, (size_t)p->M * p->M * p->M * sizeof(long long), p->stream));
+    p->spread_clean = false;
     timing_begin(p);
     SE_CUDA(se::fast_spread((const float*)xyz, (const float*)q, kp, fast_bufs(p), p->stream,
                             p->ev_cur >= 0, mark_cb, p));
     timing_mark(p, 2);
-    p->spread_clean = p->variant != 4;
     p->have_spread = true;
     p->have_scale = false;
     return SE_OK;
@@ -539,10 +540,10 @@ int graph_evaluate(se_plan* p, const void* xyz, const void* q, void* F, void* ph
         drop_graph(p);
         if (!p->cap_stream)
             SE_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
-        if (!p->spread_clean && p->variant != 3) {
+        if (!p->spread_clean) {
             const size_t M3 = (size_t)p->M * p->M * p->M;
-            if (p->variant == 4)
-                SE_CUDA(cudaMemsetAsync(p->g64, 0, M3 * sizeof(float), p->stream));
+            if (p->variant >= 3)
+                SE_CUDA(cudaMemsetAsync(p->g64, 0, M3 * sizeof(long long), p->stream));
             else
                 SE_CUDA(cudaMemsetAsync(p->grid_spread, 0, M3 * tsize(p->prec), p->stream));
             p->spread_clean = true;
@@ -831,11 +832,12 @@ int se_copy_grid(se_plan* p, int which, void* dst) {
     if (!p || !dst || (which != 0 && which != 1)) return SE_ERR_ARG;
     if (!p->ready) return SE_ERR_ARG;
     const size_t bytes = (size_t)p->M * p->M * p->M * tsize(p->prec);
+    // the single-precision pipelines clear the spread grid in the transform:
+    // it is there only between se_spread and se_scale
+    if (which == 0 && p->variant >= 3 && p->spread_clean) return SE_ERR_ARG;
     if (which == 0 && p->variant == 3)
         return check_cuda(se::fast_to_real(fast_bufs(p), p->M, (float*)dst, p->stream));
     if (which == 0 && p->variant == 4) {
-        // the float grid is cleared by the transform: only between se_spread and se_scale
-        if (p->spread_clean) return SE_ERR_ARG;
         SE_CUDA(cudaMemcpyAsync(dst, p->g64, bytes, cudaMemcpyDeviceToDevice, p->stream));
         return SE_OK;
     }

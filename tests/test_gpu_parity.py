@@ -479,3 +479,32 @@ def test_tile_gather_with_overflow():
         assert rel(phi.double().cpu().numpy(), r["phi"]) < 5 * TOL["fp32"]
         assert abs(E - r["E"]) < 5 * TOL["fp32"] * abs(r["E"])
     plan.close()
+
+
+def test_sorted_spread_is_order_independent_and_grid_lifecycle():
+    """The sorted single-precision pipeline sums the grid in integers: the
+    spread grid is bitwise the same for any order of the input particles and
+    from run to run (the bucket slots come from atomics in any order).  The
+    grid is cleared by the transform: two spreads in a row give the second
+    system's grid, and the spread grid is not available after se_scale."""
+    L, xi, M, P = 2.0, 4.0, 24, 6
+    x, q = systems.uniform_charges(700, L, seed=71, dtype=np.float32)
+    x2, q2 = systems.uniform_charges(700, L, seed=72, dtype=np.float32)
+    perm = np.random.default_rng(73).permutation(700)
+    plan = se.Plan(700, L, xi, M, P, precision="fp32", spread_variant=3, tile=6)
+    grids = []
+    for xs, qs in ((x, q), (x[perm], q[perm]), (x, q)):
+        plan.spread(torch.tensor(xs, device="cuda"), torch.tensor(qs, device="cuda"))
+        grids.append(plan.copy_grid(0).cpu().numpy())
+        plan.scale(None)
+    assert np.array_equal(grids[0], grids[1]) and np.array_equal(grids[0], grids[2])
+    with pytest.raises(nat.SEError) as e:
+        plan.copy_grid(0)
+    assert e.value.status == nat.SE_ERR_ARG
+    plan.spread(torch.tensor(x2, device="cuda"), torch.tensor(q2, device="cuda"))
+    plan.spread(torch.tensor(x, device="cuda"), torch.tensor(q, device="cuda"))
+    assert np.array_equal(plan.copy_grid(0).cpu().numpy(), grids[0])
+    r = oracle_for(x, q, L, xi, M, P, "fp32")
+    E, F, phi = plan.energy_force(torch.tensor(x, device="cuda"), torch.tensor(q, device="cuda"))
+    assert rel(F.double().cpu().numpy(), r["F"]) < 5 * TOL["fp32"]
+    plan.close()
