@@ -508,3 +508,40 @@ def test_sorted_spread_is_order_independent_and_grid_lifecycle():
     E, F, phi = plan.energy_force(torch.tensor(x, device="cuda"), torch.tensor(q, device="cuda"))
     assert rel(F.double().cpu().numpy(), r["F"]) < 5 * TOL["fp32"]
     plan.close()
+
+
+@pytest.mark.parametrize("variant", [3, 4])
+def test_empty_system_single_precision(variant):
+    plan = se.Plan(0, 2.0, 4.0, 16, 4, precision="fp32", spread_variant=variant)
+    xd = torch.empty((0, 3), dtype=torch.float32, device="cuda")
+    qd = torch.empty((0,), dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        E, F, phi = plan.energy_force(xd, qd)
+        assert E == 0.0 and F.shape == (0, 3)
+    plan.close()
+
+
+def test_largest_single_precision_grid():
+    """M = 128 (the largest grid of the single-precision pipeline: largest slab
+    shared memory, one CTA per slab), against the oracle."""
+    L, xi, M, P = 2.0, 12.0, 128, 4
+    x, q = systems.uniform_charges(2000, L, seed=81, dtype=np.float32)
+    g = run_gpu(x, q, L, xi, M, P, "fp32")
+    assert g["params"]["spread_variant"] == 3
+    r = oracle_for(x, q, L, xi, M, P, "fp32")
+    assert rel(g["F"], r["F"]) < 5 * TOL["fp32"]
+    assert rel(g["phi"], r["phi"]) < 5 * TOL["fp32"]
+    assert abs(g["E"] - r["E"]) < 5 * TOL["fp32"] * abs(r["E"])
+
+
+def test_largest_support_single_precision():
+    """P = 32 in the single-precision pipeline: a tile region of 39^3 points
+    exceeds the spread's shared-memory budget, so it is accumulated in
+    slabs of x-planes; against the oracle."""
+    L, M, P = 2.0, 40, 32
+    xi = math.sqrt(0.8 * 0.95 ** 2 * math.pi * M * M / (P * L * L))
+    x, q = systems.uniform_charges(300, L, seed=82, dtype=np.float32)
+    g = run_gpu(x, q, L, xi, M, P, "fp32", spread_variant=3, tile=8)
+    r = oracle_for(x, q, L, xi, M, P, "fp32")
+    assert rel(g["F"], r["F"]) < 5 * TOL["fp32"]
+    assert rel(g["phi"], r["phi"]) < 5 * TOL["fp32"]
