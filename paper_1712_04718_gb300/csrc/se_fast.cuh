@@ -428,10 +428,13 @@ k_fspread(const f4* __restrict__ bucket, int cap, int* __restrict__ tile_count,
     __shared__ int s_n;
     __shared__ unsigned s_qm;
     __shared__ df2 sbuf[32];
-    const int tile = blockIdx.x;
+    // CTAs 0 .. kOverflowBlocks-1 take the overflow list (scheduled first,
+    // they run beside the tiles); the others take tile blockIdx.x - kOverflowBlocks
+    const int ovf = (int)blockIdx.x < kOverflowBlocks ? (int)blockIdx.x : -1;
+    const int tile = ovf < 0 ? (int)blockIdx.x - kOverflowBlocks : kp.ntiles;
     // before the bin's results are needed: clear the first slab of this
     // tile's region and stage the Gaussian table (the CTA is scheduled early)
-    if (tile < kp.ntiles) {
+    if (ovf < 0) {
         const int nT = kp.nT, TT = kp.tile;
         const int ty = (tile / nT) % nT, tz = tile % nT, tx = tile / (nT * nT);
         const int plane = (min(TT, kp.M - ty * TT) + P - 1) * (min(TT, kp.M - tz * TT) + P - 1);
@@ -451,24 +454,24 @@ k_fspread(const f4* __restrict__ bucket, int cap, int* __restrict__ tile_count,
     const int group = (threadIdx.x >> 5) * GPW + (threadIdx.x & 31) / G;
     f4 first;
     first.x = first.y = first.z = first.w = 0.f;
-    if (tile < kp.ntiles && group < cap) first = bucket[(size_t)tile * cap + group];
+    if (ovf < 0 && group < cap) first = bucket[(size_t)tile * cap + group];
     unsigned m = 0u;
     const unsigned* qmax_b = reinterpret_cast<const unsigned*>(partials + 3 * kMaxPartials);
     for (int b = threadIdx.x; b < nbin; b += blockDim.x) m = max(m, __ldcg(qmax_b + b));
     int cnt = 0;
-    if (threadIdx.x == blockDim.x - 1) cnt = tile < kp.ntiles ? __ldcg(tile_count + tile) : __ldcg(n_over);
+    if (threadIdx.x == blockDim.x - 1) cnt = ovf < 0 ? __ldcg(tile_count + tile) : __ldcg(n_over);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     __syncthreads();
     if ((threadIdx.x & 31) == 0) atomicMax(&s_qm, m);
     if (threadIdx.x == blockDim.x - 1) {
-        if (tile < kp.ntiles) {
+        if (ovf < 0) {
             s_n = min(cnt, cap);
             tile_count[tile] = 0;   // consumed: clear for the next evaluation
         } else {
             s_n = min(cnt, kp.N);
         }
-        tile_n[min(tile, kp.ntiles)] = s_n;   // kept for the tile gather
+        tile_n[tile] = s_n;   // kept for the tile gather (the overflow count at ntiles)
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -501,7 +504,7 @@ k_fspread(const f4* __restrict__ bucket, int cap, int* __restrict__ tile_count,
     }
     const float fxs = s_fxs;
     const int n = s_n;
-    if (tile < kp.ntiles) {
+    if (ovf < 0) {
         spread_tile<P>(bucket + (size_t)tile * cap, n, g64, kp, fxs, slab, tile, sacc, sE3, true,
                        &first);
         return;
@@ -512,7 +515,7 @@ k_fspread(const f4* __restrict__ bucket, int cap, int* __restrict__ tile_count,
     const int ngroups = kOverflowBlocks * (blockDim.x >> 5) * GPW;
     (void)D;
     if (gi < GPW) {
-        for (int o = ((blockIdx.x - kp.ntiles) * (blockDim.x >> 5) + warp) * GPW + gi; o < n;
+        for (int o = (ovf * (blockDim.x >> 5) + warp) * GPW + gi; o < n;
              o += ngroups)
             spread_particle_fx<P>(wrapped[over_idx[o]], g64, kp, fxs, sE3, k);
     }
@@ -693,16 +696,17 @@ k_fgather(const f4* __restrict__ bucket, const int* __restrict__ bucket_idx, int
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gi = lane / G, k = lane - gi * G;
     const int group = warp * GPW + gi, ngroups = (blockDim.x >> 5) * GPW;
-    const int tile = blockIdx.x;
+    const int ovf = (int)blockIdx.x < kOverflowBlocks ? (int)blockIdx.x : -1;   // as k_fspread
+    const int tile = ovf < 0 ? (int)blockIdx.x - kOverflowBlocks : kp.ntiles;
     const int M = kp.M;
     // the buckets, their counts and the overflow list were written before the
     // transforms began: the first particle's factors are computed while the
     // grid is still being produced (before the dependent-launch wait)
-    const int n = tile_n[min(tile, kp.ntiles)];
+    const int n = tile_n[tile];
     df2 e_df = df_from(0.0f);
     const float gsc = adj ? (float)__ldg(adj) : 1.0f;
     const float phi_mul = gsc, F_mul = adj ? -gsc : 1.0f;
-    if (tile < kp.ntiles) {
+    if (ovf < 0) {
         const int nT = kp.nT, TT = kp.tile;
         const int t0x = (tile / (nT * nT)) * TT, t0y = ((tile / nT) % nT) * TT, t0z = (tile % nT) * TT;
         const int Rx = min(TT, M - t0x) + P - 1, Ry = min(TT, M - t0y) + P - 1,
@@ -732,7 +736,7 @@ k_fgather(const f4* __restrict__ bucket, const int* __restrict__ bucket_idx, int
             gather_emit<P>(k, valid, orig, tp.q, vphi, vfx, vfy, vfz, kp, phi, F, phi_mul, F_mul, e_df);
         }
     } else {
-        const int first = (tile - kp.ntiles) * ngroups;   // this CTA's share of the list
+        const int first = ovf * ngroups;   // this CTA's share of the list
         const int stride = kOverflowBlocks * ngroups;
         GatherPrep<float, P> gp;
         float qq = 0.0f;

@@ -114,6 +114,19 @@ cudaError_t launch_gather_pdl(const f4* sorted, const int* perm, const float* gr
                               const double* adj, cudaStream_t s);
 
 constexpr int kMaxPartials = 1024;   // blocks of the reducing kernels
+
+// Lanes per particle: a particle's P z-points are split over G = P / D lanes
+// (D points each); D is the smallest divisor of P that keeps >= 85% of the
+// warp's lanes busy.
+__host__ __device__ constexpr int pick_d(int P) {
+    for (int d = 1; d <= P; ++d) {
+        if (P % d) continue;
+        int g = P / d;
+        if (g > 32) continue;
+        if (g * (32 / g) * 100 >= 85 * 32) return d;
+    }
+    return P;
+}
 constexpr int kFastMaxM = 128;       // largest grid of the single-precision pipeline
 constexpr int kScanLimit = 8192;     // tiles scanned in shared memory
 constexpr size_t kSmemBudget = 200 * 1024;  // dynamic shared memory for a spreading tile

@@ -115,18 +115,6 @@ __device__ unsigned long long se_trace_buf[kTraceKernels][kTraceBlocks][kTracePh
     } while (0)
 #endif
 
-// Lanes per particle: a particle's P z-points are split over G = P / D lanes
-// (D points each); D is the smallest divisor of P that keeps >= 85% of the
-// warp's lanes busy.
-__host__ __device__ constexpr int pick_d(int P) {
-    for (int d = 1; d <= P; ++d) {
-        if (P % d) continue;
-        int g = P / d;
-        if (g > 32) continue;
-        if (g * (32 / g) * 100 >= 85 * 32) return d;
-    }
-    return P;
-}
 
 constexpr int kScanSmem = 8192;   // tile counts staged in shared memory by the scan
 

@@ -178,10 +178,16 @@ void derive(se_plan* p) {
     }
     if (p->prec == SE_FP32 && variant == 2) variant = 1;  // the compensated sum needs the tiles
     p->variant = variant;
-    // bucket capacity: twice the mean tile occupancy plus a margin; fuller
-    // tiles spill to the overflow list
+    // bucket capacity: twice the mean tile occupancy plus a margin, fuller
+    // tiles spilling to the overflow list; for sparse tiles (mean within 3/4
+    // of the particles one spread CTA takes per round), exactly one round, so
+    // that no tile CTA needs a second one (the rare excess goes to the
+    // overflow CTAs, which run beside the tiles)
     const int64_t mean = (p->N + p->ntiles - 1) / std::max(1, p->ntiles);
-    p->cap = (int)std::min<int64_t>(std::max<int64_t>(32, 2 * mean + 32), std::max<int64_t>(32, p->N));
+    const int64_t round = (256 / 32) * (32 / (p->P / se::pick_d(p->P)));
+    int64_t cap = std::max<int64_t>(32, 2 * mean + 32);
+    if (4 * mean <= 3 * round) cap = round;
+    p->cap = (int)std::min<int64_t>(cap, std::max<int64_t>(32, p->N));
 }
 
 void drop_graph(se_plan* p) {
