@@ -207,23 +207,32 @@ def kernel_sources_sha():
 
 def profiled_traffic(kernel, workload_name):
     """DRAM bytes per launch (read + write) of `kernel` on `workload_name` from
-    the committed ncu summary profiles/ncu_<kernel>_<workload>.md, or None
-    when there is none or it was taken on other kernel sources."""
-    path = os.path.join(ROOT, "profiles", "ncu_%s_%s.md" % (kernel, workload_name))
-    if not os.path.exists(path):
-        return None
-    vals = {}
-    for line in open(path):
-        line = line.strip().lstrip("-* ").strip()
-        if ":" in line:
-            k, v = line.split(":", 1)
-            vals[k.strip().strip("`")] = v.strip().strip("`")
-    if vals.get("kernel_sources_sha256") != kernel_sources_sha():
-        return None
-    try:
-        return float(vals["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
-        return None
+    a committed ncu summary profiles/ncu_<name>_<workload>.md: a line
+    `dram_bytes_per_launch.<kernel>: B` (or `dram_bytes_per_launch: B` in the
+    summary named for that kernel).  None when no summary holds the kernel or
+    the summary was taken on other kernel sources."""
+    import glob
+    tail = "_%s.md" % workload_name
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "ncu_*" + tail))):
+        named = os.path.basename(path)[len("ncu_"):-len(tail)]
+        vals = {}
+        for line in open(path):
+            line = line.strip().lstrip("-* ").strip()
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip().strip("`")] = v.strip().strip("`")
+        if vals.get("kernel_sources_sha256") != kernel_sources_sha():
+            continue
+        v = vals.get("dram_bytes_per_launch.%s" % kernel)
+        if v is None and named == kernel:
+            v = vals.get("dram_bytes_per_launch")
+        if v is None:
+            continue
+        try:
+            return float(v)
+        except ValueError:
+            return None
+    return None
 
 
 def roofline(kind, amount, kernel, secs, prec, peaks, workload_name):
