@@ -21,6 +21,7 @@ __all__ = [
     "build", "num_threads", "set_num_threads", "se_params", "nmax_for",
     "ewald_kspace", "ewald_structure", "ewald_eval", "ewald_real", "ewald_total",
     "se_kspace", "se_spread", "dft3", "se_scale", "se_gather",
+    "spectral_derivative", "se_kspace_ik",
 ]
 
 
@@ -57,6 +58,9 @@ def _L():
         lib.oracle_ewald_real.argtypes = [i64, p, p, d, d, d, p, p, p, p, p]
         lib.oracle_se_params.argtypes = [d, d, i, i, d, d, p]
         lib.oracle_dft3.argtypes = [p, p, i, i]
+        lib.oracle_spectral_derivative.argtypes = [p, p, i, d, i]
+        lib.oracle_se_kspace_ik.argtypes = [i64, p, p, d, d, i, i, d, d, i, p, p, p]
+        lib.oracle_se_kspace_ik.restype = i
         lib.oracle_se_spread.argtypes = [i64, p, p, d, i, i, d, d, i, p]
         lib.oracle_se_scale.argtypes = [p, p, i, d, d, d, p]
         lib.oracle_se_gather.argtypes = [i64, p, p, d, i, i, d, d, i, p, p, p]
@@ -223,3 +227,26 @@ def se_kspace(x, q, L, xi, M, P, c=0.95, eta=None, cell_mode=64, grids=False):
         out["H"] = H
         out["Ht"] = Ht
     return out
+
+
+def spectral_derivative(re, im, L, axis):
+    """Full spectrum times i k_axis (0 at the Nyquist index); returns (re, im)."""
+    re, im = _f64(re).copy(), _f64(im).copy()
+    M = re.shape[0]
+    _L().oracle_spectral_derivative(_ptr(re), _ptr(im), int(M), float(L), int(axis))
+    return re, im
+
+
+def se_kspace_ik(x, q, L, xi, M, P, c=0.95, eta=None, cell_mode=64):
+    """O2 with forces by ik differentiation (Sec. 2.3).  Returns dict(E, phi, F)."""
+    x, q = _f64(x), _f64(q)
+    N = len(q)
+    phi = np.zeros(N)
+    F = np.zeros((N, 3))
+    E = ctypes.c_double()
+    rc = _L().oracle_se_kspace_ik(N, _ptr(x), _ptr(q), float(L), float(xi), int(M), int(P),
+                                  float(c), float(eta) if eta else 0.0, int(cell_mode),
+                                  ctypes.byref(E), _ptr(phi), _ptr(F))
+    if rc:
+        raise MemoryError("oracle_se_kspace_ik")
+    return dict(E=E.value, phi=phi, F=F)

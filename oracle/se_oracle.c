@@ -24,6 +24,9 @@
  *       separable, FP64 twiddles), scaling by the modified Green's function
  *       (Eq. 3.6), inverse DFT, and gather of potential and force with the
  *       same Gaussian (Eq. 3.9, 3.13).
+ *       With forces by ik differentiation (Sec. 2.3) instead, the scaled
+ *       spectrum is also multiplied by i k_d and transformed back per axis,
+ *       and the gather applies the plain window to those derivative grids.
  *
  * Readings of the paper taken here (each also listed in the design notes):
  *  - Force = -dE/dx exactly (Eq. 1.3 first equality).  Eq. 1.7 and 3.13 carry
@@ -531,6 +534,77 @@ void oracle_se_gather(int64_t N, const double *x, const double *q, double L,
         F[3 * n + 1] = -2.0 * alpha * h3 * q[n] * fy;
         F[3 * n + 2] = -2.0 * alpha * h3 * q[n] * fz;
     }
+}
+
+/* Differentiation by i k in Fourier space (Sec. 2.3, the first of the three
+ * ways to obtain the force): a full M^3 spectrum (iz fastest) is multiplied
+ * by i k_d, k_d = 2 pi n_d / L with n_d the signed index along axis d.  For
+ * an even M the Nyquist index n_d = M/2 stands for both +M/2 and -M/2; it
+ * gets k_d = 0 (reading: the derivative of that mode is not defined on the
+ * grid, and 0 keeps the derivative of a real grid real). */
+void oracle_spectral_derivative(double *re, double *im, int M, double L, int axis)
+{
+    const double t = 2.0 * M_PI / L;
+    for (int nx = 0; nx < M; ++nx)
+        for (int ny = 0; ny < M; ++ny)
+            for (int nz = 0; nz < M; ++nz) {
+                int n = axis == 0 ? nx : (axis == 1 ? ny : nz);
+                int sn = (2 * n == M) ? 0 : signed_index(n, M);
+                double k = t * sn;
+                size_t i = ((size_t)nx * M + ny) * M + nz;
+                double a = re[i], b = im[i];
+                re[i] = -k * b;
+                im[i] = k * a;
+            }
+}
+
+/*
+ * SE k-space evaluation with forces by ik differentiation (Sec. 2.3): spread,
+ * DFT and scaling as oracle_se_kspace; then, per axis d, the scaled spectrum
+ * times i k_d, inverse DFT (the d-derivative of the smoothed potential grid),
+ * and the gather with the same window as the spread (Eq. 3.9):
+ *   F_m,d = -q_m h^3 sum_j (d_d Ht)_j c_g exp(-alpha |x_j - x_m|^2),
+ * i.e. F = -q grad phi with the derivative taken on the grid instead of on
+ * the window.  phi and E as in oracle_se_kspace.
+ */
+int oracle_se_kspace_ik(int64_t N, const double *x, const double *q,
+                        double L, double xi, int M, int P, double c, double eta_in,
+                        int cell_mode, double *E, double *phi, double *F)
+{
+    double prm[6];
+    oracle_se_params(L, xi, M, P, c, eta_in, prm);
+    const double eta = prm[2], alpha = prm[3], cg = prm[4];
+    const size_t M3 = (size_t)M * M * M;
+    double *re = (double *)malloc(sizeof(double) * M3);
+    double *im = (double *)calloc(M3, sizeof(double));
+    double *dr = (double *)malloc(sizeof(double) * M3);
+    double *di = (double *)malloc(sizeof(double) * M3);
+    double *gd = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    double *Fs = (double *)malloc(sizeof(double) * 3 * (size_t)(N > 0 ? N : 1));
+    if (!re || !im || !dr || !di || !gd || !Fs) {
+        free(re); free(im); free(dr); free(di); free(gd); free(Fs);
+        return -1;
+    }
+    oracle_se_spread(N, x, q, L, M, P, alpha, cg, cell_mode, re);
+    oracle_dft3(re, im, M, -1);
+    double eg = 0.0;
+    oracle_se_scale(re, im, M, L, xi, eta, &eg);
+    for (int d = 0; d < 3; ++d) {
+        memcpy(dr, re, sizeof(double) * M3);
+        memcpy(di, im, sizeof(double) * M3);
+        oracle_spectral_derivative(dr, di, M, L, d);
+        oracle_dft3(dr, di, M, +1);
+        /* the phi output of the gather on the derivative grid is h^3 sum D W */
+        oracle_se_gather(N, x, q, L, M, P, alpha, cg, cell_mode, dr, gd, Fs);
+        for (int64_t n = 0; n < N; ++n) F[3 * n + d] = -q[n] * gd[n];
+    }
+    oracle_dft3(re, im, M, +1);
+    oracle_se_gather(N, x, q, L, M, P, alpha, cg, cell_mode, re, phi, Fs);
+    double e = 0.0;
+    for (int64_t n = 0; n < N; ++n) e += 0.5 * q[n] * phi[n];
+    *E = e;
+    free(re); free(im); free(dr); free(di); free(gd); free(Fs);
+    return 0;
 }
 
 /*
