@@ -407,6 +407,7 @@ def run_ours(args):
         if prec != "fp64" and w["M"] <= 128:
             out["unsorted_variant"] = unsorted_variant(se, torch, x, q, w, prec, min(K, 1000), flush)
         out["autograd"] = autograd_timing(se, torch, x, q, w, prec, max(20, min(K, 500)), flush)
+        out["modes"] = other_modes(se, torch, x, q, w, prec, min(K, 500), flush, (variant, tile))
         out["cpu_baseline"] = cpu_baseline(x, q, w, args.cpu_seconds)
     plan.close()
     if ws > 1:
@@ -651,6 +652,45 @@ def unsorted_variant(se, torch, x, q, w, prec, K, flush):
     ms = sum(a.elapsed_time(b) for a, b in zip(st, en)) / K
     return {"spread_variant": 4, "value": 1e3 / ms, "unit": "evals/s", "ms_per_step": ms,
             "steps": K}
+
+
+def other_modes(se, torch, x, q, w, prec, K, flush, cfg):
+    """The workload in the evaluation modes beside the headline's: forces by
+    ik differentiation (the cuFFT pipeline with three more inverse FFTs and a
+    four-grid gather), potential only (the gather without force sums) and
+    energy only (no gather).  Same timing as the headline."""
+    N = len(q)
+    _, Fref, _ = reference_forces(se, torch, x, q, w)
+    out = {}
+    for mode in ("ik_forces", "potential_only", "energy_only"):
+        plan = se.Plan(N, w["L"], w["xi"], w["M"], w["P"], precision=prec,
+                       force_mode="ik" if mode == "ik_forces" else "analytic")
+        if prec != "fp64":
+            plan.set_tuning(*cfg)
+        dt = plan.dtype
+        xd = torch.tensor(x, dtype=dt, device="cuda")
+        qd = torch.tensor(q, dtype=dt, device="cuda")
+        F = torch.empty((N, 3), dtype=dt, device="cuda") if mode == "ik_forces" else None
+        phi = torch.empty((N,), dtype=dt, device="cuda") if mode != "energy_only" else None
+        Ed = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for _ in range(10):
+            plan.evaluate(xd, qd, F, phi, Ed)
+        st = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        en = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        for i in range(K):
+            flush()
+            st[i].record()
+            plan.evaluate(xd, qd, F, phi, Ed)
+            en[i].record()
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in zip(st, en)) / K
+        r = {"value": 1e3 / ms, "unit": "evals/s", "ms_per_step": ms, "steps": K,
+             "spread_variant": int(plan.params()["spread_variant"])}
+        if F is not None:
+            r["rel_rms_force_err"] = rel_rms(F.double().cpu().numpy(), Fref)
+        out[mode] = r
+        plan.close()
+    return out
 
 
 def no_graph(se, torch, plan, xd, qd, F, phi, Ed, flush, K):

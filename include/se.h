@@ -109,6 +109,25 @@ int se_plan_set_tuning(se_plan *plan, int spread_variant, int tile);
  * c_g = (2 xi^2 / (pi eta))^{3/2} is the Gaussian's normalisation (Eq. 3.5). */
 int se_plan_get_params(const se_plan *plan, double *out);
 
+/* How the gather obtains the force (Sec. 2.3 lists three ways; the paper's
+ * SE uses the first below):
+ *   SE_FORCE_ANALYTIC (default): the derivative of the window (Sec. 3.1),
+ *     F = -dE/dx of the discrete SE energy exactly; one inverse FFT.
+ *   SE_FORCE_IK: differentiation by i k in Fourier space.  The scaling step
+ *     also forms D_d = i k_d G(k)/M^3 Hhat (d = x, y, z; k_d = 2 pi n_d / L
+ *     with n_d the signed index, 0 at the Nyquist index of an even M), three
+ *     more inverse FFTs give the gradient grids, and the gather applies the
+ *     plain window: F_m,d = -kc q_m h^3 sum_j D_d,j W(x_j - x_m).  These
+ *     forces conserve momentum (sum_m F_m = 0 to rounding) but are not the
+ *     exact derivative of the energy.  They are evaluated by the cuFFT
+ *     pipeline (spread variant 1 or 2; a tuning of 3 or 4 is overridden),
+ *     with 3 M^3 more real and 3 M^2 (M/2+1) more complex values of grid
+ *     memory.  Potentials, energies and se_adjoint are the same in both modes.
+ * Returns SE_ERR_ARG for another mode.  Takes effect at the next call. */
+#define SE_FORCE_ANALYTIC 0
+#define SE_FORCE_IK 1
+int se_plan_set_force_mode(se_plan *plan, int mode);
+
 /* Step (a) of Algorithm 1 with the SE window (Eq. 3.5): sort particles into
  * grid tiles and spread H_j = sum_n q_n c_g exp(-alpha |x_j - x_n|^2) onto
  * the plan's real grid (M^3, z fastest).  xyz, q: device. */
@@ -127,7 +146,10 @@ int se_scale(se_plan *plan, double *E_grid);
  *   F_m   = -kc 2 alpha h^3 q_m sum_j (x_j - x_m) Ht_j c_g exp(-alpha |x_j - x_m|^2)
  * F_m is -dE/dx_m of the discrete SE energy.  Requires se_spread (with the
  * same xyz, q) and se_scale.  phi, F and E (device pointer to one double,
- * E = 1/2 sum q phi) may each be NULL. */
+ * E = 1/2 sum q phi) may each be NULL.  With F NULL the gather runs with the
+ * plain window alone (potential-only mode: about half the arithmetic of the
+ * gather with forces).  With SE_FORCE_IK, F is the ik force (see
+ * se_plan_set_force_mode). */
 int se_gather(se_plan *plan, const void *xyz, const void *q, void *phi, void *F,
               double *E);
 
@@ -143,14 +165,16 @@ int se_adjoint(se_plan *plan, const void *xyz, const void *q, const double *gE,
 
 /* The whole k-space evaluation: se_spread, se_scale, se_gather.  E is a HOST
  * pointer (the call waits for the stream); F and phi are device pointers and
- * may be NULL.  Returns SE_WARN_NONNEUTRAL for a non-neutral system and
+ * may be NULL.  With both NULL (energy-only mode) the gather is skipped and E
+ * is the grid energy of se_scale, equal to 1/2 sum q phi to rounding.  Returns SE_WARN_NONNEUTRAL for a non-neutral system and
  * SE_ERR_NONFINITE for NaN/Inf input. */
 int se_energy_force(se_plan *plan, const void *xyz, const void *q, double *E,
                     void *F, void *phi);
 
 /* The whole evaluation with every result on the device and no host
  * synchronisation: F, phi and E (one double, E = 1/2 sum q phi) are device
- * pointers and may each be NULL.  Status checks (non-neutral, non-finite)
+ * pointers and may each be NULL; F and phi both NULL is the energy-only mode
+ * of se_energy_force.  Status checks (non-neutral, non-finite)
  * are kept on the device; read them with se_plan_get_status. */
 int se_evaluate(se_plan *plan, const void *xyz, const void *q, void *F, void *phi,
                 double *E);

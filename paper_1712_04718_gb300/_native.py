@@ -22,6 +22,8 @@ SE_ERR_NONFINITE = -6
 SE_FP64 = 0
 SE_FP32 = 1
 SE_FP32_PLAIN = 2
+SE_FORCE_ANALYTIC = 0
+SE_FORCE_IK = 1
 SE_PROBE_FP32_FMA = 0
 SE_PROBE_FP64_FMA = 1
 SE_PROBE_SMEM_ATOMIC_U32 = 2
@@ -38,6 +40,7 @@ SIGNATURES = {
     "se_plan_set_prefactor": (_i, [_vp, _d]),
     "se_plan_set_stream": (_i, [_vp, _vp]),
     "se_plan_set_tuning": (_i, [_vp, _i, _i]),
+    "se_plan_set_force_mode": (_i, [_vp, _i]),
     "se_plan_get_params": (_i, [_vp, _dp]),
     "se_spread": (_i, [_vp, _vp, _vp]),
     "se_scale": (_i, [_vp, _vp]),

@@ -72,6 +72,22 @@ cudaError_t launch_gather(const v4_t<T>* sorted, const int* perm, const T* grid,
                           Acc* acc, double e_scale, double* E_out, const double* adj,
                           cudaStream_t s);
 
+// ik differentiation (se_plain.cuh): scale as launch_scale, and in addition
+// D_d = i k_d G/M^3 Hhat into dgrid (d = x, y, z; each an M x M x (M/2+1)
+// complex half spectrum, dstride >= M^2 (M/2+1) complex values apart).
+template <typename T>
+cudaError_t launch_scale_ik(void* cgrid, void* dgrid, size_t dstride, const double* green, int M,
+                            double L, T* zero_grid, double* partials, unsigned* ticket, Acc* acc,
+                            double e_scale, double* E_out, cudaStream_t s);
+// Gather with the underived window from ng grids gstride values apart:
+// ng = 1 potential (and energy) only; ng = 4 potential and ik forces from
+// [Ht, dHt/dx, dHt/dy, dHt/dz].  pdl: launched as a programmatic dependent.
+template <typename T>
+cudaError_t launch_gather_plain(int ng, const v4_t<T>* sorted, const int* perm, const T* grid,
+                                size_t gstride, T* phi, T* F, const KParams<T>& kp,
+                                double* partials, unsigned* ticket, Acc* acc, double e_scale,
+                                double* E_out, bool pdl, cudaStream_t s);
+
 // Kernel parameters for an FP64 evaluation without a plan (se_plan.cu).
 int make_kparams_f64(int64_t N, double L, double xi, int M, int P, int tile, KParams<double>* out);
 

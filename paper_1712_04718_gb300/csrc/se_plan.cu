@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/se.h"
@@ -41,6 +42,7 @@ struct se_plan {
     double kc = 1.0;
     cudaStream_t stream = nullptr;
     int tune_variant = 0, tune_tile = 0;
+    int force_mode = SE_FORCE_ANALYTIC;
 
     // derived (set by derive())
     double h = 0, w = 0, eta = 0, alpha = 0, cg = 0, m = 0;
@@ -50,9 +52,13 @@ struct se_plan {
     // device state (prepare())
     bool ready = false;
     int ready_prec = -1;
+    int ready_force = -1;
     int device = -1;
     void* grid_spread = nullptr;   // M^3 real: spread output, FFT input
-    void* grid_gather = nullptr;   // M^3 real: inverse FFT output, gather input
+    void* grid_gather = nullptr;   // M^3 real: inverse FFT output, gather input; with ik
+                                   // forces 4 grids ik_gstride apart: Ht, then its x, y, z
+                                   // derivatives
+    void* cgrid_ik = nullptr;      // ik forces: 3 spectra ik_cstride apart, i k_d G/M^3 Hhat
     void* cgrid = nullptr;         // M x M x (M/2+1) complex
     double* green = nullptr;       // G(k) on the half spectrum (FP64)
     int* tile_count = nullptr;
@@ -153,6 +159,12 @@ void timing_mark(se_plan* p, int s) {
 
 size_t tsize(int prec) { return prec == SE_FP64 ? sizeof(double) : sizeof(float); }
 
+// Spacing of the four real grids (values) and of the three derivative spectra
+// (complex values) of ik forces: M^3 and M^2 (M/2+1) rounded up so that every
+// grid starts on a 256-byte boundary (an odd M^3 would not).
+size_t ik_gstride(const se_plan* p) { return ((size_t)p->M * p->M * p->M + 63) & ~(size_t)63; }
+size_t ik_cstride(const se_plan* p) { return ((size_t)p->M * p->M * (p->M / 2 + 1) + 31) & ~(size_t)31; }
+
 // Sec. 3 and Eq. 4.2: h = L/M, w = P h / 2, m = c sqrt(pi P),
 // eta = (2 w xi / m)^2, alpha = 2 xi^2 / eta, c_g = (2 xi^2 / (pi eta))^{3/2}.
 void derive(se_plan* p) {
@@ -172,9 +184,11 @@ void derive(se_plan* p) {
     int variant = p->tune_variant;
     if (variant == 3 && !fast_ok) variant = 0;
     if (variant == 4 && (p->prec == SE_FP64 || p->M > se::kFastMaxM)) variant = 0;
+    // ik forces need the three extra inverse transforms of the cuFFT pipeline
+    if (p->force_mode == SE_FORCE_IK && variant >= 3) variant = 0;
     if (variant == 0) {
         if (p->prec == SE_FP64) variant = p->P > 12 ? 2 : 1;
-        else variant = fast_ok ? 3 : 1;
+        else variant = (fast_ok && p->force_mode != SE_FORCE_IK) ? 3 : 1;
     }
     if (p->prec == SE_FP32 && variant == 2) variant = 1;  // the compensated sum needs the tiles
     p->variant = variant;
@@ -205,11 +219,12 @@ void release_device(se_plan* p) {
     void* bufs[] = {p->grid_spread, p->grid_gather, p->cgrid, p->green, p->tile_count,
                     p->tile_start, p->slot, p->tile_of, p->perm, p->sorted, p->partials,
                     p->tickets, p->acc, p->dE, p->h_xyz, p->h_q, p->h_F, p->h_phi, p->g64, p->tw, p->green_f,
-                    p->bucket, p->bucket_idx};
+                    p->bucket, p->bucket_idx, p->cgrid_ik};
     for (void* b : bufs)
         if (b) cudaFree(b);
     p->grid_spread = p->grid_gather = p->cgrid = p->sorted = p->tw = p->bucket = nullptr;
     p->bucket_idx = nullptr;
+    p->cgrid_ik = nullptr;
     p->g64 = nullptr;
     p->green_f = nullptr;
     p->green = p->partials = p->dE = nullptr;
@@ -219,6 +234,7 @@ void release_device(se_plan* p) {
     p->h_xyz = p->h_q = p->h_F = p->h_phi = nullptr;
     p->ready = false;
     p->ready_prec = -1;
+    p->ready_force = -1;
 }
 
 int dalloc(void** ptr, size_t bytes) {
@@ -278,7 +294,8 @@ std::vector<double> green_table(const se_plan* p) {
 int prepare(se_plan* p) {
     int dev = 0;
     SE_CUDA(cudaGetDevice(&dev));
-    if (p->ready && p->ready_prec == p->prec && p->device == dev) return SE_OK;
+    if (p->ready && p->ready_prec == p->prec && p->ready_force == p->force_mode && p->device == dev)
+        return SE_OK;
     release_device(p);
     derive(p);
     p->device = dev;
@@ -287,6 +304,7 @@ int prepare(se_plan* p) {
     const size_t nc = (size_t)p->M * p->M * (p->M / 2 + 1);
     const size_t N = (size_t)p->N;
     const bool fast = p->variant >= 3;
+    const bool ik = p->force_mode == SE_FORCE_IK;
     int rc = SE_OK;
     if (rc == SE_OK && !fast) rc = dalloc(&p->grid_spread, M3 * ts);
     if (rc == SE_OK && fast) rc = dalloc((void**)&p->g64, M3 * sizeof(long long));
@@ -296,7 +314,8 @@ int prepare(se_plan* p) {
         rc = dalloc((void**)&p->bucket_idx, (size_t)p->ntiles * p->cap * sizeof(int));
     if (rc == SE_OK && fast) rc = dalloc(&p->tw, (size_t)p->M * 2 * sizeof(float));
     if (rc == SE_OK && fast) rc = dalloc((void**)&p->green_f, nc * sizeof(float));
-    if (rc == SE_OK) rc = dalloc(&p->grid_gather, M3 * ts);
+    if (rc == SE_OK) rc = dalloc(&p->grid_gather, ik ? 4 * ik_gstride(p) * ts : M3 * ts);
+    if (rc == SE_OK && ik) rc = dalloc(&p->cgrid_ik, 3 * ik_cstride(p) * 2 * ts);
     if (rc == SE_OK) rc = dalloc(&p->cgrid, nc * 2 * ts);
     if (rc == SE_OK) rc = dalloc((void**)&p->green, nc * sizeof(double));
     if (rc == SE_OK) rc = dalloc((void**)&p->tile_count, (size_t)p->ntiles * sizeof(int));
@@ -349,6 +368,7 @@ int prepare(se_plan* p) {
         p->have_spread = p->have_scale = false;
         p->ready = true;
         p->ready_prec = p->prec;
+        p->ready_force = p->force_mode;
         return SE_OK;
     }
     const cufftType tf = p->prec == SE_FP64 ? CUFFT_D2Z : CUFFT_R2C;
@@ -367,6 +387,7 @@ int prepare(se_plan* p) {
     p->have_spread = p->have_scale = false;
     p->ready = true;
     p->ready_prec = p->prec;
+    p->ready_force = p->force_mode;
     return SE_OK;
 }
 
@@ -430,10 +451,19 @@ int fast_scale(se_plan* p, double* E_grid) {
 
 int fast_gather(se_plan* p, void* phi, void* F, double* E, const double* adj = nullptr) {
     const KParams<float> kp = make_kparams<float>(p);
-    if (p->variant == 3 && se::fast_gather_tiled(kp)) {
+    if (p->variant == 3 && (F || adj) && se::fast_gather_tiled(kp)) {
         SE_CUDA(se::fast_gather(kp, fast_bufs(p), (float*)phi, (float*)F,
                                 p->partials + 4 * se::kMaxPartials, p->tickets + 2, 0.5, E, adj,
                                 p->stream));
+        timing_mark(p, 6);
+        return SE_OK;
+    }
+    if (!F && !adj) {   // potential (and energy) only: the plain window
+        SE_CUDA(se::launch_gather_plain<float>(1, (const se::f4*)p->sorted, nullptr,
+                                               (const float*)p->grid_gather,
+                                               (size_t)p->M * p->M * p->M, (float*)phi, nullptr, kp,
+                                               p->partials + 4 * se::kMaxPartials, p->tickets + 2,
+                                               p->acc, 0.5, E, true, p->stream));
         timing_mark(p, 6);
         return SE_OK;
     }
@@ -482,14 +512,29 @@ int do_scale(se_plan* p, double* E_grid) {
     timing_mark(p, 3);
     const double M3 = (double)p->M * p->M * p->M;
     const double e_scale = p->kc * p->h * p->h * p->h / (2.0 * M3);
-    SE_CUDA(se::launch_scale<T>(p->cgrid, p->green, p->M, (T*)p->grid_spread, p->partials + 3 * se::kMaxPartials,
-                                p->tickets + 1, p->acc, e_scale, E_grid, p->stream));
+    const bool ik = p->force_mode == SE_FORCE_IK;
+    if (ik)
+        SE_CUDA(se::launch_scale_ik<T>(p->cgrid, p->cgrid_ik, ik_cstride(p), p->green, p->M, p->L,
+                                       (T*)p->grid_spread,
+                                       p->partials + 3 * se::kMaxPartials, p->tickets + 1, p->acc,
+                                       e_scale, E_grid, p->stream));
+    else
+        SE_CUDA(se::launch_scale<T>(p->cgrid, p->green, p->M, (T*)p->grid_spread, p->partials + 3 * se::kMaxPartials,
+                                    p->tickets + 1, p->acc, e_scale, E_grid, p->stream));
     timing_mark(p, 4);
     p->spread_clean = true;
-    if (p->prec == SE_FP64)
-        SE_CUFFT(cufftExecZ2D(p->inv, (cufftDoubleComplex*)p->cgrid, (cufftDoubleReal*)p->grid_gather));
-    else
-        SE_CUFFT(cufftExecC2R(p->inv, (cufftComplex*)p->cgrid, (cufftReal*)p->grid_gather));
+    // Ht, then (ik forces) the three derivative grids, each by the plan's
+    // inverse transform from a 256-byte aligned spectrum to an aligned grid
+    using C = typename std::conditional<std::is_same<T, float>::value, cufftComplex,
+                                        cufftDoubleComplex>::type;
+    for (int d = 0; d < (ik ? 4 : 1); ++d) {
+        C* src = d == 0 ? (C*)p->cgrid : (C*)p->cgrid_ik + (size_t)(d - 1) * ik_cstride(p);
+        T* dst = (T*)p->grid_gather + (size_t)d * ik_gstride(p);
+        if (p->prec == SE_FP64)
+            SE_CUFFT(cufftExecZ2D(p->inv, (cufftDoubleComplex*)src, (cufftDoubleReal*)dst));
+        else
+            SE_CUFFT(cufftExecC2R(p->inv, (cufftComplex*)src, (cufftReal*)dst));
+    }
     timing_mark(p, 5);
     p->have_scale = true;
     return SE_OK;
@@ -499,11 +544,29 @@ template <typename T>
 int do_gather(se_plan* p, void* phi, void* F, double* E, const double* adj = nullptr) {
     const KParams<T> kp = make_kparams<T>(p);
     using V = se::v4_t<T>;
-    SE_CUDA(se::launch_gather<T>((const V*)p->sorted, p->perm, (const T*)p->grid_gather, (T*)phi,
-                                 (T*)F, kp, p->partials + 4 * se::kMaxPartials, p->tickets + 2,
-                                 p->acc, 0.5, E, adj, p->stream));
+    // ik forces: potential and force from the four grids with the plain window;
+    // no forces asked for: the plain window on Ht alone; else (and for the
+    // adjoint, which needs the analytic derivative) the analytic gather
+    const int ng = adj ? 0 : (p->force_mode == SE_FORCE_IK && F ? 4 : (F ? 0 : 1));
+    if (ng > 0)
+        SE_CUDA(se::launch_gather_plain<T>(ng, (const V*)p->sorted, p->perm, (const T*)p->grid_gather,
+                                           ik_gstride(p), (T*)phi, (T*)F, kp,
+                                           p->partials + 4 * se::kMaxPartials, p->tickets + 2,
+                                           p->acc, 0.5, E, false, p->stream));
+    else
+        SE_CUDA(se::launch_gather<T>((const V*)p->sorted, p->perm, (const T*)p->grid_gather, (T*)phi,
+                                     (T*)F, kp, p->partials + 4 * se::kMaxPartials, p->tickets + 2,
+                                     p->acc, 0.5, E, adj, p->stream));
     timing_mark(p, 6);
     return SE_OK;
+}
+
+// E^L read back from the device results: 1/2 sum q phi from the gather, or in
+// the energy-only mode (no gather) the grid energy kc h^3/(2 M^3) sum_k w G |Hhat|^2.
+double energy_from_acc(const se_plan* p, const Acc& a, bool energy_only) {
+    if (!energy_only) return 0.5 * a.e_gather;
+    const double M3 = (double)p->M * p->M * p->M;
+    return p->kc * p->h * p->h * p->h / (2.0 * M3) * a.e_grid;
 }
 
 int status_from_acc(const Acc& a) {
@@ -512,21 +575,24 @@ int status_from_acc(const Acc& a) {
     return SE_OK;
 }
 
+// Energy only (F and phi both NULL): no gather; E is the grid energy of the
+// scaling step, equal to 1/2 sum q phi to rounding (Parseval).
 int evaluate(se_plan* p, const void* xyz, const void* q, void* F, void* phi, double* dE) {
+    const bool energy_only = !F && !phi;
     if (p->variant >= 3) {
         SE_TRY(fast_spread(p, xyz, q));
-        SE_TRY(fast_scale(p, nullptr));
-        SE_TRY(fast_gather(p, phi, F, dE));
+        SE_TRY(fast_scale(p, energy_only ? dE : nullptr));
+        if (!energy_only) SE_TRY(fast_gather(p, phi, F, dE));
         return SE_OK;
     }
     if (p->prec == SE_FP64) {
         SE_TRY(do_spread<double>(p, xyz, q));
-        SE_TRY(do_scale<double>(p, nullptr));
-        SE_TRY(do_gather<double>(p, phi, F, dE));
+        SE_TRY(do_scale<double>(p, energy_only ? dE : nullptr));
+        if (!energy_only) SE_TRY(do_gather<double>(p, phi, F, dE));
     } else {
         SE_TRY(do_spread<float>(p, xyz, q));
-        SE_TRY(do_scale<float>(p, nullptr));
-        SE_TRY(do_gather<float>(p, phi, F, dE));
+        SE_TRY(do_scale<float>(p, energy_only ? dE : nullptr));
+        if (!energy_only) SE_TRY(do_gather<float>(p, phi, F, dE));
     }
     return SE_OK;
 }
@@ -723,6 +789,14 @@ int se_plan_set_tuning(se_plan* p, int spread_variant, int tile) {
     return SE_OK;
 }
 
+int se_plan_set_force_mode(se_plan* p, int mode) {
+    if (!p || (mode != SE_FORCE_ANALYTIC && mode != SE_FORCE_IK)) return SE_ERR_ARG;
+    if (mode == p->force_mode) return SE_OK;
+    p->force_mode = mode;
+    invalidate(p);
+    return SE_OK;
+}
+
 int se_plan_get_params(const se_plan* p, double* out) {
     if (!p || !out) return SE_ERR_ARG;
     out[0] = p->h;
@@ -776,7 +850,7 @@ int se_energy_force(se_plan* p, const void* xyz, const void* q, double* E, void*
         Acc a;
         SE_CUDA(cudaMemcpyAsync(&a, p->acc, sizeof(Acc), cudaMemcpyDeviceToHost, p->stream));
         SE_CUDA(cudaStreamSynchronize(p->stream));
-        *E = 0.5 * a.e_gather;
+        *E = energy_from_acc(p, a, !F && !phi);
         return status_from_acc(a);
     }
     return SE_OK;
@@ -804,7 +878,7 @@ int se_energy_force_host(se_plan* p, const void* xyz, const void* q, double* E, 
     Acc a;
     SE_CUDA(cudaMemcpyAsync(&a, p->acc, sizeof(Acc), cudaMemcpyDeviceToHost, p->stream));
     SE_CUDA(cudaStreamSynchronize(p->stream));
-    if (E) *E = 0.5 * a.e_gather;
+    if (E) *E = energy_from_acc(p, a, !F && !phi);
     return status_from_acc(a);
 }
 

@@ -12,6 +12,7 @@ import torch
 from . import _native as nat
 
 PRECISIONS = {"fp64": nat.SE_FP64, "fp32": nat.SE_FP32, "fp32plain": nat.SE_FP32_PLAIN}
+FORCE_MODES = {"analytic": nat.SE_FORCE_ANALYTIC, "ik": nat.SE_FORCE_IK}
 _TORCH_DTYPE = {nat.SE_FP64: torch.float64, nat.SE_FP32: torch.float32,
                 nat.SE_FP32_PLAIN: torch.float32}
 _NP_DTYPE = {nat.SE_FP64: np.float64, nat.SE_FP32: np.float32, nat.SE_FP32_PLAIN: np.float32}
@@ -26,10 +27,12 @@ class Plan:
 
     precision: "fp64" (every step in double) or "fp32" (single precision with
     compensated grid sums; FP64 Green's function table and energy reduction).
+    force_mode: "analytic" (derivative of the window, Sec. 3.1) or "ik"
+    (differentiation in Fourier space, Sec. 2.3; see se_plan_set_force_mode).
     """
 
     def __init__(self, N, L, xi, M, P, precision="fp64", c=None, eta=None,
-                 prefactor=None, spread_variant=0, tile=0):
+                 prefactor=None, spread_variant=0, tile=0, force_mode="analytic"):
         if not torch.cuda.is_available():
             raise RuntimeError("libse needs a CUDA device; none is available")
         self._lib = nat.load()
@@ -49,6 +52,9 @@ class Plan:
         if spread_variant or tile:
             nat.check(self._lib.se_plan_set_tuning(self._h, int(spread_variant), int(tile)),
                       "se_plan_set_tuning")
+        self.force_mode = nat.SE_FORCE_ANALYTIC
+        if force_mode != "analytic":
+            self.set_force_mode(force_mode)
         self.last_status = 0
         # counts evaluations that overwrite the plan's grids (spreads); the
         # autograd layer uses it to know whether the grid of a forward pass
@@ -130,6 +136,30 @@ class Plan:
         self.last_status = nat.check(st, "se_energy_force")
         return E.value, F, phi
 
+    def energy(self, xyz, q):
+        """Energy-only mode: E (python float) from the grid energy, no gather."""
+        self._check_inputs(xyz, q)
+        self._stream()
+        self.generation += 1
+        E = ctypes.c_double()
+        st = self._lib.se_energy_force(self._h, _ptr(xyz), _ptr(q), ctypes.byref(E), None, None)
+        self.last_status = nat.check(st, "se_energy_force")
+        return E.value
+
+    def potential(self, xyz, q, phi=None):
+        """Potential-only mode: E (python float) and phi [N] with the plain window
+        (no force sums)."""
+        self._check_inputs(xyz, q)
+        if phi is None:
+            phi = torch.empty((self.N,), dtype=self.dtype, device=xyz.device)
+        self._stream()
+        self.generation += 1
+        E = ctypes.c_double()
+        st = self._lib.se_energy_force(self._h, _ptr(xyz), _ptr(q), ctypes.byref(E), None,
+                                       _ptr(phi))
+        self.last_status = nat.check(st, "se_energy_force")
+        return E.value, phi
+
     def energy_force_host(self, xyz, q):
         """Host (numpy) in, host out: copies to the device, evaluates, copies back."""
         xyz = np.ascontiguousarray(xyz, dtype=self.np_dtype)
@@ -202,6 +232,12 @@ class Plan:
         """Spreading variant (0 automatic, 1-4 as in se_plan_set_tuning) and tile edge."""
         nat.check(self._lib.se_plan_set_tuning(self._h, int(spread_variant), int(tile)),
                   "se_plan_set_tuning")
+
+    def set_force_mode(self, mode):
+        """"analytic" or "ik" (or SE_FORCE_ANALYTIC / SE_FORCE_IK)."""
+        m = FORCE_MODES[mode] if isinstance(mode, str) else int(mode)
+        nat.check(self._lib.se_plan_set_force_mode(self._h, m), "se_plan_set_force_mode")
+        self.force_mode = m
 
     def copy_grid(self, which):
         """0: spread grid H (valid after spread), 1: Ht (after scale); [M,M,M] tensor."""

@@ -62,6 +62,15 @@ def test_argument_validation(lib):
     assert lib.se_plan_set_tuning(h, 4, 0) == nat.SE_ERR_UNSUPPORTED
     assert lib.se_plan_set_precision(h, nat.SE_FP32) == nat.SE_OK
     assert lib.se_plan_set_tuning(h, 2, 0) == nat.SE_ERR_UNSUPPORTED  # direct spread is FP64 only
+    # force mode: ik differentiation moves the FP32 plan to the cuFFT pipeline
+    assert lib.se_plan_set_force_mode(h, 2) == nat.SE_ERR_ARG
+    assert lib.se_plan_set_force_mode(None, nat.SE_FORCE_IK) == nat.SE_ERR_ARG
+    prm = (ctypes.c_double * 10)()
+    assert lib.se_plan_get_params(h, prm) == nat.SE_OK and prm[7] == 3
+    assert lib.se_plan_set_force_mode(h, nat.SE_FORCE_IK) == nat.SE_OK
+    assert lib.se_plan_get_params(h, prm) == nat.SE_OK and prm[7] == 1
+    assert lib.se_plan_set_force_mode(h, nat.SE_FORCE_ANALYTIC) == nat.SE_OK
+    assert lib.se_plan_get_params(h, prm) == nat.SE_OK and prm[7] == 3
     # compute calls before any spread are rejected without touching the device
     assert lib.se_scale(h, None) == nat.SE_ERR_ARG
     assert lib.se_gather(h, None, None, None, None, None) == nat.SE_ERR_ARG
