@@ -266,6 +266,39 @@ int se_spread_noalloc(const double *xyz, const double *q, int64_t N, double L, d
                       int M, int P, double *H, void *stream);
 
 /* Static message for a status code. */
+/* ---- Parameter selection (host only; no device is touched) ----
+ * For an absolute rms error tolerance tol of the potential, the energy or
+ * the force (quantity), a real-space cut-off rc, the box L and
+ * Q = sum_n q_n^2, following the paper's estimates:
+ *   xi     from the real-space truncation estimate (Eq. 2.3: through W0
+ *          for the potential and energy, a logarithm for the force);
+ *   k_inf  from the Fourier-space truncation estimate (Eq. 2.4) and
+ *          M = 2 ceil(k_inf) (Sec. 3);
+ *   P      the smallest even P with A e^{-pi P c^2/2} <= tol (Sec. 4:
+ *          A = sqrt(Q xi L)/L, Q sqrt(xi L)/L, 4 pi Q sqrt(xi^3/L) for the
+ *          potential, energy and force); M is raised where needed so that
+ *          eta of Eq. 4.2 stays at most 1/2 (the bounds fail near eta = 1),
+ *          and to P, and rounded up to even.
+ * c: the shape constant of Eq. 4.2 (0 selects 0.95).  Writes *xi, *M, *P
+ * and, if k_inf is not NULL, the unrounded k_inf.  Returns SE_ERR_ARG for a
+ * non-positive or non-finite tol, rc, L or Q, or an unknown quantity;
+ * SE_ERR_UNSUPPORTED when the tolerance is met with no Fourier part or the
+ * selected P exceeds 32 (the outputs are still written in that case). */
+#define SE_QUANTITY_POTENTIAL 0
+#define SE_QUANTITY_ENERGY 1
+#define SE_QUANTITY_FORCE 2
+int se_select_params(int quantity, double tol, double rc, double L, double Q, double c,
+                     double *xi, int *M, int *P, double *k_inf);
+
+/* The even support P >= 2 with e^{-pi P c^2/2} <= scaled_tol, the error
+ * relative to the bound's constant A (Sec. 4; c = 0 selects 0.95), or
+ * SE_ERR_ARG for a non-positive scaled_tol or negative c. */
+int se_select_support(double scaled_tol, double c);
+
+/* The principal branch W0 of the Lambert function (w e^w = z) for z >= 0,
+ * NaN otherwise: the inverse the estimates of Eq. 2.3-2.4 need. */
+double se_lambert_w0(double z);
+
 const char *se_strerror(int status);
 
 /* Stage timing (tracing).  enable = 1 records a CUDA event before and after

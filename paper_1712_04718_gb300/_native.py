@@ -22,6 +22,9 @@ SE_ERR_NONFINITE = -6
 SE_FP64 = 0
 SE_FP32 = 1
 SE_FP32_PLAIN = 2
+SE_QUANTITY_POTENTIAL = 0
+SE_QUANTITY_ENERGY = 1
+SE_QUANTITY_FORCE = 2
 SE_FORCE_ANALYTIC = 0
 SE_FORCE_IK = 1
 SE_PROBE_FP32_FMA = 0
@@ -67,6 +70,10 @@ SIGNATURES = {
     "se_batch_get_status": (_i, [_vp, ctypes.POINTER(_i)]),
     "se_batch_autotune": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i, _i, ctypes.POINTER(_i),
                                ctypes.POINTER(ctypes.c_float)]),
+    "se_select_params": (_i, [_i, _d, _d, _d, _d, _d, _dp, ctypes.POINTER(_i),
+                              ctypes.POINTER(_i), _dp]),
+    "se_select_support": (_i, [_d, _d]),
+    "se_lambert_w0": (_d, [_d]),
     "se_strerror": (ctypes.c_char_p, [_i]),
     "se_probe_peak": (_i, [_i, ctypes.POINTER(_d)]),
     "se_version": (_i, []),

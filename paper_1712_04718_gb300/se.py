@@ -254,6 +254,38 @@ class Plan:
         return E.value
 
 
+QUANTITIES = {"potential": nat.SE_QUANTITY_POTENTIAL, "energy": nat.SE_QUANTITY_ENERGY,
+              "force": nat.SE_QUANTITY_FORCE}
+
+
+def select_params(quantity, tol, rc, L, Q, c=0.95):
+    """se_select_params (host only, no device needed): xi, M, P for an absolute
+    rms error tol of "potential", "energy" or "force" with real-space cut-off
+    rc, box L and Q = sum q^2.  Returns dict(xi, M, P, k_inf, supported);
+    supported is False when P would exceed 32 or no Fourier part is needed."""
+    lib = nat.load()
+    xi, kinf = ctypes.c_double(), ctypes.c_double()
+    M, P = ctypes.c_int(), ctypes.c_int()
+    qn = QUANTITIES[quantity] if isinstance(quantity, str) else int(quantity)
+    st = lib.se_select_params(qn, float(tol), float(rc), float(L), float(Q), float(c),
+                              ctypes.byref(xi), ctypes.byref(M), ctypes.byref(P),
+                              ctypes.byref(kinf))
+    if st == nat.SE_ERR_UNSUPPORTED:
+        return dict(xi=xi.value, M=M.value, P=P.value, k_inf=kinf.value, supported=False)
+    nat.check(st, "se_select_params")
+    return dict(xi=xi.value, M=M.value, P=P.value, k_inf=kinf.value, supported=True)
+
+
+def select_support(scaled_tol, c=0.95):
+    """se_select_support: smallest even P with e^{-pi P c^2/2} <= scaled_tol."""
+    return nat.check(nat.load().se_select_support(float(scaled_tol), float(c)),
+                     "se_select_support")
+
+
+def lambert_w0(z):
+    return nat.load().se_lambert_w0(float(z))
+
+
 # C-ABI names, for callers who want the flat interface.
 def se_plan_create(N, L, xi, M, P, **kw):
     return Plan(N, L, xi, M, P, **kw)
