@@ -266,6 +266,33 @@ int se_spread_noalloc(const double *xyz, const double *q, int64_t N, double L, d
                       int M, int P, double *H, void *stream);
 
 /* Static message for a status code. */
+/* ---- Real-space part of the Ewald sum (the complement of the k-space path) ----
+ * Sec. 1, Eq. 1.5-1.7: for charges in [0, L)^3 with splitting parameter xi
+ * and cut-off rc (0 < rc <= L/3):
+ *   phi_m = kc [ sum over particles n and periodic images with 0 < r < rc of
+ *                q_n erfc(xi r)/r  -  2 xi/sqrt(pi) q_m ]
+ *   F_m   = kc q_m sum_{r < rc} q_n (2 xi/sqrt(pi) e^{-xi^2 r^2} + erfc(xi r)/r)
+ *           (x_m - x_n)/r^2            (the image of x_n at distance r)
+ *   E     = 1/2 sum q_m phi_m  (real-space energy plus the self energy)
+ * Added to se_evaluate's k-space results they give the whole Ewald potential,
+ * force and energy.  Cells of edge >= rc (L/rc per dimension, at most 40) hold
+ * the particles; rc > L/3 returns SE_ERR_UNSUPPORTED at creation.
+ * se_real_evaluate: xyz [N][3], q [N], F [N][3], phi [N] DEVICE arrays of the
+ * precision's type (SE_FP64 double, SE_FP32 float), E a DEVICE double; F,
+ * phi and E may be NULL.  accumulate = 0 overwrites the outputs, 1 adds to
+ * them (F += ..., phi += ..., *E += ...).  Asynchronous on the stream.  The
+ * order of the additions inside a cell follows atomic slot claims, so results
+ * are reproducible to rounding, not bitwise. */
+typedef struct se_real se_real;
+int se_real_create(se_real **out, int64_t N, double L, double xi, double rc);
+int se_real_destroy(se_real *real);
+int se_real_set_precision(se_real *real, int prec);   /* SE_FP64 (default) or SE_FP32 */
+int se_real_set_prefactor(se_real *real, double kc);
+int se_real_set_stream(se_real *real, void *stream);
+int se_real_get_cells(const se_real *real, int *cells_per_dim);
+int se_real_evaluate(se_real *real, const void *xyz, const void *q, void *F, void *phi,
+                     double *E, int accumulate);
+
 /* ---- Parameter selection (host only; no device is touched) ----
  * For an absolute rms error tolerance tol of the potential, the energy or
  * the force (quantity), a real-space cut-off rc, the box L and

@@ -21,7 +21,7 @@ __all__ = [
     "build", "num_threads", "set_num_threads", "se_params", "nmax_for",
     "ewald_kspace", "ewald_structure", "ewald_eval", "ewald_real", "ewald_total",
     "se_kspace", "se_spread", "dft3", "se_scale", "se_gather",
-    "spectral_derivative", "se_kspace_ik",
+    "spectral_derivative", "se_kspace_ik", "ewald_real_at",
 ]
 
 
@@ -56,6 +56,7 @@ def _L():
         lib.oracle_ewald_kspace.argtypes = [i64, p, p, d, d, i, p, p, p]
         lib.oracle_ewald_kspace.restype = i
         lib.oracle_ewald_real.argtypes = [i64, p, p, d, d, d, p, p, p, p, p]
+        lib.oracle_ewald_real_at.argtypes = [i64, p, p, d, d, d, i64, p, p, p]
         lib.oracle_se_params.argtypes = [d, d, i, i, d, d, p]
         lib.oracle_dft3.argtypes = [p, p, i, i]
         lib.oracle_spectral_derivative.argtypes = [p, p, i, d, i]
@@ -153,6 +154,17 @@ def ewald_real(x, q, L, xi, rc):
                            _ptr(F))
     return dict(E_real=Er.value, E_self=Es.value, phi_real=phi, phi_self=phis,
                 F_real=F)
+
+
+def ewald_real_at(x, q, L, xi, rc, idx):
+    """O1 real-space phi (self term excluded) and F at the particles idx."""
+    x, q = _f64(x), _f64(q)
+    idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+    phi = np.zeros(len(idx))
+    F = np.zeros((len(idx), 3))
+    _L().oracle_ewald_real_at(len(q), _ptr(x), _ptr(q), float(L), float(xi), float(rc),
+                              len(idx), idx.ctypes.data_as(ctypes.c_void_p), _ptr(phi), _ptr(F))
+    return phi, F
 
 
 def ewald_total(x, q, L, xi, tol=1e-16):

@@ -315,6 +315,40 @@ int oracle_ewald_kspace(int64_t N, const double *x, const double *q,
  *   E^S     = 1/2 sum_m q_m phi^S_m,  E^self = -xi/sqrt(pi) sum_m q_m^2
  * phi and F receive the real-space part; phi_self receives the self term.
  */
+/* The real-space potential and force of oracle_ewald_real at T target
+ * particles idx[t] only (same images, same cut-off, same terms; the self
+ * term not included): for checks of large systems on a sample. */
+void oracle_ewald_real_at(int64_t N, const double *x, const double *q,
+                          double L, double xi, double rc, int64_t T,
+                          const int64_t *idx, double *phi, double *F)
+{
+    const int pmax = (int)ceil(rc / L) + 1;
+    const double twoxi_sqrtpi = 2.0 * xi / sqrt(M_PI);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t t = 0; t < T; ++t) {
+        const int64_t m = idx[t];
+        double ph = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
+        for (int64_t n = 0; n < N; ++n)
+            for (int px = -pmax; px <= pmax; ++px)
+                for (int py = -pmax; py <= pmax; ++py)
+                    for (int pz = -pmax; pz <= pmax; ++pz) {
+                        if (n == m && px == 0 && py == 0 && pz == 0) continue;
+                        double dx = x[3 * m] - x[3 * n] + px * L;
+                        double dy = x[3 * m + 1] - x[3 * n + 1] + py * L;
+                        double dz = x[3 * m + 2] - x[3 * n + 2] + pz * L;
+                        double r2 = dx * dx + dy * dy + dz * dz;
+                        if (r2 > rc * rc) continue;
+                        double r = sqrt(r2);
+                        double ec = erfc(xi * r) / r;
+                        ph += q[n] * ec;
+                        double s = q[n] * (twoxi_sqrtpi * exp(-xi * xi * r2) + ec) / r2;
+                        fx += s * dx; fy += s * dy; fz += s * dz;
+                    }
+        phi[t] = ph;
+        F[3 * t] = q[m] * fx; F[3 * t + 1] = q[m] * fy; F[3 * t + 2] = q[m] * fz;
+    }
+}
+
 void oracle_ewald_real(int64_t N, const double *x, const double *q,
                        double L, double xi, double rc,
                        double *E_real, double *E_self,

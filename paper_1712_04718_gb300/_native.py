@@ -70,6 +70,13 @@ SIGNATURES = {
     "se_batch_get_status": (_i, [_vp, ctypes.POINTER(_i)]),
     "se_batch_autotune": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i, _i, ctypes.POINTER(_i),
                                ctypes.POINTER(ctypes.c_float)]),
+    "se_real_create": (_i, [ctypes.POINTER(_vp), _i64, _d, _d, _d]),
+    "se_real_destroy": (_i, [_vp]),
+    "se_real_set_precision": (_i, [_vp, _i]),
+    "se_real_set_prefactor": (_i, [_vp, _d]),
+    "se_real_set_stream": (_i, [_vp, _vp]),
+    "se_real_get_cells": (_i, [_vp, ctypes.POINTER(_i)]),
+    "se_real_evaluate": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i]),
     "se_select_params": (_i, [_i, _d, _d, _d, _d, _d, _dp, ctypes.POINTER(_i),
                               ctypes.POINTER(_i), _dp]),
     "se_select_support": (_i, [_d, _d]),

@@ -14,7 +14,8 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libse.so")
 SOURCES = ["se_plan.cu", "se_kernels_f32.cu", "se_kernels_f64.cu", "se_noalloc.cu",
            "se_kernels_fast.cu", "se_batch.cu", "se_probe.cu",
-           "se_plain_f32.cu", "se_plain_f64.cu", "se_select.cu"]
+           "se_plain_f32.cu", "se_plain_f64.cu", "se_select.cu",
+           "se_real.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -1,0 +1,445 @@
+// se_real.cu -- the real-space part of the Ewald sum on the GPU, with cell
+// lists: the complement of the SE k-space path for full Ewald energies and
+// forces (Sec. 1, Eq. 1.5-1.7, the erfc terms and the self term).
+//
+// For charges q_n at x_n in the periodic box [0, L)^3, splitting parameter
+// xi and cut-off r_c:
+//   phi_m = kc [ sum_{n, images; 0 < r < r_c} q_n erfc(xi r) / r  -  2 xi / sqrt(pi) q_m ]
+//   F_m   = kc q_m sum_{n, images; r < r_c} q_n (2 xi / sqrt(pi) e^{-xi^2 r^2} + erfc(xi r) / r)
+//           (x_m - x_n^image) / r^2
+//   E     = 1/2 sum_m q_m phi_m            (real-space energy plus the self energy)
+// so that these plus the k-space results of se_evaluate are the whole Ewald
+// potential, force and energy.
+//
+// GPU design: particles are counted into cells of edge >= r_c (nc = floor(L
+// / r_c) per dimension, nc >= 3, so the 27 neighbour cells of a cell are 27
+// distinct periodic images and every pair within r_c is met exactly once),
+// scanned and scattered into cell order.  One CTA per home cell stages the
+// 27 neighbour cells in shared memory with their image shift applied (in
+// chunks when they do not fit), and each home particle's candidate loop is
+// split over S adjacent lanes (S a power of two, S x home particles <= the
+// CTA), reduced by shuffles.  Every particle sums its own potential and
+// force: no atomics on the outputs.  The energy is a deterministic two-level
+// reduction (last block).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "../../include/se.h"
+#include "se_internal.h"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxCellsPerDim = 40;     // at most 64 000 cells (one energy partial each)
+constexpr size_t kNbSmem = 64 * 1024;   // shared memory for staged neighbours
+
+template <typename T> struct R4 { using type = se::v4_t<T>; };
+
+__device__ __forceinline__ float erfcT(float a) { return erfcf(a); }
+__device__ __forceinline__ double erfcT(double a) { return erfc(a); }
+__device__ __forceinline__ float expR(float a) { return expf(a); }
+__device__ __forceinline__ double expR(double a) { return exp(a); }
+__device__ __forceinline__ float sqrtR(float a) { return sqrtf(a); }
+__device__ __forceinline__ double sqrtR(double a) { return sqrt(a); }
+__device__ __forceinline__ float floorR(float a) { return floorf(a); }
+__device__ __forceinline__ double floorR(double a) { return floor(a); }
+
+// Wrap into [0, L): x - L floor(x / L), then one correction; NaN or anything
+// still outside becomes 0.
+template <typename T>
+__device__ __forceinline__ T wrapR(T x, T L, T invL) {
+    if (x >= T(0) && x < L) return x;
+    T y = x - L * floorR(x * invL);
+    if (y >= L) y -= L;
+    if (!(y >= T(0) && y < L)) y = T(0);
+    return y;
+}
+
+template <typename T>
+__device__ __forceinline__ int cellR(T x, T cscale, int nc) {
+    int c = (int)(x * cscale);
+    return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_rs_count(const T* __restrict__ xyz, int N, T L, T invL, T cscale, int nc, int* count,
+           int* __restrict__ cell_of, int* __restrict__ slot) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int cx = cellR(wrapR(xyz[3 * i], L, invL), cscale, nc);
+    const int cy = cellR(wrapR(xyz[3 * i + 1], L, invL), cscale, nc);
+    const int cz = cellR(wrapR(xyz[3 * i + 2], L, invL), cscale, nc);
+    const int c = (cx * nc + cy) * nc + cz;
+    cell_of[i] = c;
+    slot[i] = atomicAdd(&count[c], 1);
+}
+
+// Exclusive scan of the cell counts into start[0..ncells] by one CTA of 1024
+// threads, chunk by chunk with a running carry; the counts are cleared for
+// the next evaluation.
+__global__ void __launch_bounds__(1024) k_rs_scan(int* count, int* start, int ncells) {
+    __shared__ int wsum[32];
+    __shared__ int carry_s;
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int base = 0; base < ncells; base += 1024) {
+        const int i = base + threadIdx.x;
+        const int v = i < ncells ? count[i] : 0;
+        if (i < ncells) count[i] = 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int w = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        const int carry = carry_s;
+        const int incl = x + (warp > 0 ? wsum[warp - 1] : 0);
+        if (i < ncells) start[i] = carry + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry_s = carry + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) start[ncells] = carry_s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_rs_scatter(const T* __restrict__ xyz, const T* __restrict__ q, int N, T L, T invL,
+             const int* __restrict__ cell_of, const int* __restrict__ slot,
+             const int* __restrict__ start, typename R4<T>::type* __restrict__ sorted,
+             int* __restrict__ perm) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int p = start[cell_of[i]] + slot[i];
+    typename R4<T>::type v;
+    v.x = wrapR(xyz[3 * i], L, invL);
+    v.y = wrapR(xyz[3 * i + 1], L, invL);
+    v.z = wrapR(xyz[3 * i + 2], L, invL);
+    v.w = q[i];
+    sorted[p] = v;
+    perm[p] = i;
+}
+
+__device__ __forceinline__ double block_sum_d(double v, double* sbuf) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sbuf[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (warp == 0) {
+        r = lane < (int)(blockDim.x >> 5) ? sbuf[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    return r;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_rs_pairs(const typename R4<T>::type* __restrict__ sorted, const int* __restrict__ start,
+           const int* __restrict__ perm, int nc, T L, T rc2, T xi, T c2xi, T kc, int cap,
+           T* __restrict__ phi, T* __restrict__ F, int accumulate, double* __restrict__ partials,
+           unsigned* ticket, double* E_out) {
+    using V = typename R4<T>::type;
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    V* nb = reinterpret_cast<V*>(smem_raw);
+    __shared__ double sbuf[32];
+    __shared__ bool last;
+    const int cid = blockIdx.x;
+    const int cx = cid / (nc * nc), cy = (cid / nc) % nc, cz = cid % nc;
+    const int h0 = start[cid], nh = start[cid + 1] - h0;
+    int S = 1;
+    while (S < 32 && 2 * S * nh <= (int)blockDim.x) S <<= 1;
+    const int per_pass = blockDim.x / S;
+    const int s = threadIdx.x % S;
+    double e_loc = 0.0;
+    for (int pass0 = 0; pass0 < nh; pass0 += per_pass) {
+        const int li = pass0 + threadIdx.x / S;
+        const bool act = li < nh;
+        V me;
+        me.x = me.y = me.z = me.w = T(0);
+        if (act) me = sorted[h0 + li];
+        T ph = T(0), fx = T(0), fy = T(0), fz = T(0);
+        // stream the 27 neighbour cells through shared memory, cap at a time
+        int k = 0, koff = 0;
+        while (k < 27) {
+            int filled = 0;
+            __syncthreads();
+            while (k < 27 && filled < cap) {
+                const int dx = k / 9 - 1, dy = (k / 3) % 3 - 1, dz = k % 3 - 1;
+                int nx = cx + dx, ny = cy + dy, nz = cz + dz;
+                T sx = T(0), sy = T(0), sz = T(0);
+                if (nx < 0) { nx += nc; sx = -L; } else if (nx >= nc) { nx -= nc; sx = L; }
+                if (ny < 0) { ny += nc; sy = -L; } else if (ny >= nc) { ny -= nc; sy = L; }
+                if (nz < 0) { nz += nc; sz = -L; } else if (nz >= nc) { nz -= nc; sz = L; }
+                const int nid = (nx * nc + ny) * nc + nz;
+                const int b0 = start[nid], cnt = start[nid + 1] - b0;
+                const int take = min(cnt - koff, cap - filled);
+                for (int t = threadIdx.x; t < take; t += blockDim.x) {
+                    V v = sorted[b0 + koff + t];
+                    v.x += sx;
+                    v.y += sy;
+                    v.z += sz;
+                    nb[filled + t] = v;
+                }
+                filled += take;
+                koff += take;
+                if (koff == cnt) {
+                    ++k;
+                    koff = 0;
+                }
+            }
+            __syncthreads();
+            if (act) {
+                // 32 candidates per lane at a time: distance tests into a bit
+                // mask, then the erfc terms of the hits only (a warp then pays
+                // for its largest hit count, not for every candidate)
+                for (int j0 = s; j0 < filled; j0 += 32 * S) {
+                    unsigned mask = 0u;
+#pragma unroll 8
+                    for (int b = 0; b < 32; ++b) {
+                        const int j = j0 + b * S;
+                        if (j < filled) {
+                            const V n = nb[j];
+                            const T dx = me.x - n.x, dy = me.y - n.y, dz = me.z - n.z;
+                            const T r2 = dx * dx + dy * dy + dz * dz;
+                            if (r2 < rc2 && r2 > T(0)) mask |= 1u << b;
+                        }
+                    }
+                    while (mask) {
+                        const int b = __ffs(mask) - 1;
+                        mask &= mask - 1u;
+                        const V n = nb[j0 + b * S];
+                        const T dx = me.x - n.x, dy = me.y - n.y, dz = me.z - n.z;
+                        const T r2 = dx * dx + dy * dy + dz * dz;
+                        const T r = sqrtR(r2);
+                        const T ir = T(1) / r;
+                        const T ec = erfcT(xi * r) * ir;
+                        ph += n.w * ec;
+                        const T f = n.w * (c2xi * expR(-xi * xi * r2) + ec) * ir * ir;
+                        fx += f * dx;
+                        fy += f * dy;
+                        fz += f * dz;
+                    }
+                }
+            }
+        }
+        // sum over the S lanes of each particle (adjacent lanes, aligned groups)
+        for (int o = S >> 1; o > 0; o >>= 1) {
+            ph += __shfl_xor_sync(0xffffffffu, ph, o);
+            fx += __shfl_xor_sync(0xffffffffu, fx, o);
+            fy += __shfl_xor_sync(0xffffffffu, fy, o);
+            fz += __shfl_xor_sync(0xffffffffu, fz, o);
+        }
+        if (act && s == 0) {
+            const T pm = kc * (ph - c2xi * me.w);
+            const T fq = kc * me.w;
+            const int o = perm[h0 + li];
+            if (phi) phi[o] = accumulate ? phi[o] + pm : pm;
+            if (F) {
+                if (accumulate) {
+                    F[3 * o] += fq * fx;
+                    F[3 * o + 1] += fq * fy;
+                    F[3 * o + 2] += fq * fz;
+                } else {
+                    F[3 * o] = fq * fx;
+                    F[3 * o + 1] = fq * fy;
+                    F[3 * o + 2] = fq * fz;
+                }
+            }
+            e_loc += (double)me.w * (double)pm;
+        }
+    }
+    const double r = block_sum_d(e_loc, sbuf);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = r;
+        __threadfence();
+        const unsigned t = atomicAdd(ticket, 1u);
+        last = t == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double e = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) e += partials[b];
+    e = block_sum_d(e, sbuf);
+    if (threadIdx.x == 0) {
+        if (E_out) *E_out = accumulate ? *E_out + 0.5 * e : 0.5 * e;
+        *ticket = 0u;
+    }
+}
+
+}  // namespace
+
+struct se_real {
+    int64_t N = 0;
+    double L = 0, xi = 0, rc = 0, kc = 1.0;
+    int prec = SE_FP64;
+    cudaStream_t stream = nullptr;
+    int nc = 0, ncells = 0;
+    bool ready = false;
+    int ready_prec = -1;
+    int* count = nullptr;
+    int* start = nullptr;
+    int* cell_of = nullptr;
+    int* slot = nullptr;
+    int* perm = nullptr;
+    void* sorted = nullptr;
+    double* partials = nullptr;
+    unsigned* ticket = nullptr;
+};
+
+namespace {
+
+void rs_release(se_real* r) {
+    void* b[] = {r->count, r->start, r->cell_of, r->slot, r->perm, r->sorted, r->partials, r->ticket};
+    for (void* p : b)
+        if (p) cudaFree(p);
+    r->count = r->start = r->cell_of = r->slot = r->perm = nullptr;
+    r->sorted = nullptr;
+    r->partials = nullptr;
+    r->ticket = nullptr;
+    r->ready = false;
+}
+
+int rs_alloc(void** p, size_t bytes) {
+    return cudaMalloc(p, bytes ? bytes : 16) == cudaSuccess ? SE_OK : SE_ERR_NOMEM;
+}
+
+int rs_prepare(se_real* r) {
+    if (r->ready && r->ready_prec == r->prec) return SE_OK;
+    rs_release(r);
+    const size_t N = (size_t)r->N, ts = r->prec == SE_FP64 ? 8 : 4;
+    int rc = SE_OK;
+    if (rc == SE_OK) rc = rs_alloc((void**)&r->count, (size_t)r->ncells * sizeof(int));
+    if (rc == SE_OK) rc = rs_alloc((void**)&r->start, ((size_t)r->ncells + 1) * sizeof(int));
+    if (rc == SE_OK) rc = rs_alloc((void**)&r->cell_of, N * sizeof(int));
+    if (rc == SE_OK) rc = rs_alloc((void**)&r->slot, N * sizeof(int));
+    if (rc == SE_OK) rc = rs_alloc((void**)&r->perm, N * sizeof(int));
+    if (rc == SE_OK) rc = rs_alloc(&r->sorted, N * 4 * ts);
+    if (rc == SE_OK) rc = rs_alloc((void**)&r->partials, (size_t)r->ncells * sizeof(double));
+    if (rc == SE_OK) rc = rs_alloc((void**)&r->ticket, sizeof(unsigned));
+    if (rc == SE_OK && (cudaMemset(r->count, 0, (size_t)r->ncells * sizeof(int)) != cudaSuccess ||
+                        cudaMemset(r->ticket, 0, sizeof(unsigned)) != cudaSuccess))
+        rc = SE_ERR_CUDA;
+    if (rc != SE_OK) {
+        rs_release(r);
+        return rc;
+    }
+    r->ready = true;
+    r->ready_prec = r->prec;
+    return SE_OK;
+}
+
+template <typename T>
+int rs_run(se_real* r, const void* xyz, const void* q, void* F, void* phi, double* E, int acc) {
+    using V = typename R4<T>::type;
+    const int N = (int)r->N, nc = r->nc;
+    const T L = (T)r->L, invL = (T)(1.0 / r->L), cscale = (T)(nc / r->L);
+    const int nb = (N + kThreads - 1) / kThreads;
+    cudaStream_t s = r->stream;
+    k_rs_count<T><<<nb, kThreads, 0, s>>>((const T*)xyz, N, L, invL, cscale, nc, r->count,
+                                          r->cell_of, r->slot);
+    k_rs_scan<<<1, 1024, 0, s>>>(r->count, r->start, r->ncells);
+    k_rs_scatter<T><<<nb, kThreads, 0, s>>>((const T*)xyz, (const T*)q, N, L, invL, r->cell_of,
+                                            r->slot, r->start, (V*)r->sorted, r->perm);
+    const int cap = (int)(kNbSmem / sizeof(V));
+    if (cudaFuncSetAttribute(k_rs_pairs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kNbSmem) != cudaSuccess)
+        return SE_ERR_CUDA;
+    const double c2xi = 2.0 * r->xi / sqrt(3.14159265358979323846);
+    k_rs_pairs<T><<<r->ncells, kThreads, kNbSmem, s>>>(
+        (const V*)r->sorted, r->start, r->perm, nc, L, (T)(r->rc * r->rc), (T)r->xi, (T)c2xi,
+        (T)r->kc, cap, (T*)phi, (T*)F, acc, r->partials, r->ticket, E);
+    return cudaGetLastError() == cudaSuccess ? SE_OK : SE_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" int se_real_create(se_real** out, int64_t N, double L, double xi, double rc) {
+    if (!out) return SE_ERR_ARG;
+    *out = nullptr;
+    if (N < 0 || N >= ((int64_t)1 << 31) || !(L > 0.0) || !isfinite(L) || !(xi > 0.0) ||
+        !isfinite(xi) || !(rc > 0.0) || !isfinite(rc))
+        return SE_ERR_ARG;
+    const double cells = floor(L / rc);
+    if (cells < 3.0) return SE_ERR_UNSUPPORTED;   // r_c > L/3
+    se_real* r = new (std::nothrow) se_real;
+    if (!r) return SE_ERR_NOMEM;
+    r->N = N;
+    r->L = L;
+    r->xi = xi;
+    r->rc = rc;
+    r->nc = (int)std::min<double>(cells, kMaxCellsPerDim);
+    r->ncells = r->nc * r->nc * r->nc;
+    *out = r;
+    return SE_OK;
+}
+
+extern "C" int se_real_destroy(se_real* r) {
+    if (!r) return SE_OK;
+    rs_release(r);
+    delete r;
+    return SE_OK;
+}
+
+extern "C" int se_real_set_precision(se_real* r, int prec) {
+    if (!r || (prec != SE_FP64 && prec != SE_FP32)) return SE_ERR_ARG;
+    r->prec = prec;
+    return SE_OK;
+}
+
+extern "C" int se_real_set_prefactor(se_real* r, double kc) {
+    if (!r || !(kc > 0.0) || !isfinite(kc)) return SE_ERR_ARG;
+    r->kc = kc;
+    return SE_OK;
+}
+
+extern "C" int se_real_set_stream(se_real* r, void* stream) {
+    if (!r) return SE_ERR_ARG;
+    r->stream = (cudaStream_t)stream;
+    return SE_OK;
+}
+
+extern "C" int se_real_get_cells(const se_real* r, int* cells_per_dim) {
+    if (!r || !cells_per_dim) return SE_ERR_ARG;
+    *cells_per_dim = r->nc;
+    return SE_OK;
+}
+
+extern "C" int se_real_evaluate(se_real* r, const void* xyz, const void* q, void* F, void* phi,
+                                double* E, int accumulate) {
+    if (!r || (r->N > 0 && (!xyz || !q))) return SE_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SE_ERR_CUDA;
+    int rc = rs_prepare(r);
+    if (rc != SE_OK) return rc;
+    if (r->N == 0) {
+        if (E && !accumulate && cudaMemsetAsync(E, 0, sizeof(double), r->stream) != cudaSuccess)
+            return SE_ERR_CUDA;
+        return SE_OK;
+    }
+    return r->prec == SE_FP64 ? rs_run<double>(r, xyz, q, F, phi, E, accumulate)
+                              : rs_run<float>(r, xyz, q, F, phi, E, accumulate);
+}

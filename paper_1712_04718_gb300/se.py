@@ -254,6 +254,55 @@ class Plan:
         return E.value
 
 
+class RealSpace:
+    """Real-space part of the Ewald sum with cell lists (se_real_*): phi, F and
+    E of the erfc terms within rc plus the self term, on the GPU; added to a
+    Plan's k-space results they give the whole Ewald sum."""
+
+    def __init__(self, N, L, xi, rc, precision="fp64", prefactor=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libse needs a CUDA device; none is available")
+        self._lib = nat.load()
+        self._h = ctypes.c_void_p()
+        nat.check(self._lib.se_real_create(ctypes.byref(self._h), int(N), float(L), float(xi),
+                                           float(rc)), "se_real_create")
+        self.N = int(N)
+        self.prec = PRECISIONS[precision]
+        if self.prec == nat.SE_FP32_PLAIN:
+            self.prec = nat.SE_FP32
+        nat.check(self._lib.se_real_set_precision(self._h, self.prec), "se_real_set_precision")
+        if prefactor is not None:
+            nat.check(self._lib.se_real_set_prefactor(self._h, float(prefactor)),
+                      "se_real_set_prefactor")
+
+    @property
+    def dtype(self):
+        return _TORCH_DTYPE[self.prec]
+
+    def cells_per_dim(self):
+        n = ctypes.c_int()
+        nat.check(self._lib.se_real_get_cells(self._h, ctypes.byref(n)), "se_real_get_cells")
+        return n.value
+
+    def evaluate(self, xyz, q, F=None, phi=None, E=None, accumulate=False):
+        """Device tensors (plan dtype); E: CUDA float64 tensor of one element."""
+        s = torch.cuda.current_stream().cuda_stream
+        nat.check(self._lib.se_real_set_stream(self._h, ctypes.c_void_p(s)), "se_real_set_stream")
+        nat.check(self._lib.se_real_evaluate(self._h, _ptr(xyz), _ptr(q), _ptr(F), _ptr(phi),
+                                             _ptr(E), int(bool(accumulate))), "se_real_evaluate")
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.se_real_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 QUANTITIES = {"potential": nat.SE_QUANTITY_POTENTIAL, "energy": nat.SE_QUANTITY_ENERGY,
               "force": nat.SE_QUANTITY_FORCE}
 

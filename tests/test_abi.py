@@ -82,6 +82,25 @@ def test_argument_validation(lib):
     assert lib.se_probe_peak(0, None) == nat.SE_ERR_ARG
 
 
+def test_real_space_arguments(lib):
+    """se_real_create validates its arguments on the host; the cell grid is
+    floor(L / rc) per dimension, at most 40; rc > L/3 is not supported."""
+    from paper_1712_04718_gb300 import _native as nat
+    h = ctypes.c_void_p()
+    for args in ((-1, 3.0, 3.0, 1.0), (10, 0.0, 3.0, 1.0), (10, 3.0, -1.0, 1.0),
+                 (10, 3.0, 3.0, 0.0), (10, float("inf"), 3.0, 1.0)):
+        assert lib.se_real_create(ctypes.byref(h), *args) == nat.SE_ERR_ARG, args
+    assert lib.se_real_create(ctypes.byref(h), 10, 3.0, 3.0, 1.01) == nat.SE_ERR_UNSUPPORTED
+    n = ctypes.c_int()
+    for L, rc, cells in ((3.0, 1.0, 3), (6.0, 1.0, 6), (10.0, 0.9, 11), (100.0, 1.0, 40)):
+        assert lib.se_real_create(ctypes.byref(h), 10, L, 3.0, rc) == nat.SE_OK
+        assert lib.se_real_get_cells(h, ctypes.byref(n)) == nat.SE_OK and n.value == cells
+        assert lib.se_real_set_precision(h, 5) == nat.SE_ERR_ARG
+        assert lib.se_real_set_prefactor(h, -1.0) == nat.SE_ERR_ARG
+        assert lib.se_real_destroy(h) == nat.SE_OK
+    assert lib.se_real_destroy(None) == nat.SE_OK
+
+
 @pytest.mark.parametrize("L,xi,M,P", [(3.0, 3.5, 32, 16), (6.0, 3.12, 52, 6), (10.0, 3.12, 84, 8)])
 def test_derived_parameters_match_oracle(lib, L, xi, M, P):
     """h, w, eta (Eq. 4.2), alpha and c_g of the library equal the oracle's."""

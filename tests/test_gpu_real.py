@@ -1,0 +1,159 @@
+"""GPU parity of the real-space Ewald sum (se_real_*) against the oracle's
+image sum O1 (Sec. 1, Eq. 1.5-1.7), and of the whole Ewald sum (k-space plan
+plus real space) against the converged Ewald total.
+
+Tolerances: FP64 1e-12 relative normwise (rounding only).  FP32: each of the
+~400 terms within the cut-off (|q erfc(xi r)/r| up to ~10 at the closest
+pairs) carries a few ulp (erfcf, expf, the products): about
+sqrt(400) x 10 x 3e-7 = 6e-5 absolute against potentials and forces of order
+1-10, so 5e-5 relative normwise."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1712_04718_gb300 import _native as nat
+from paper_1712_04718_gb300 import se, systems
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 5e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    n = math.sqrt((b ** 2).sum())
+    d = math.sqrt(((a - b) ** 2).sum())
+    return d / n if n > 0 else d
+
+
+def run_real(x, q, L, xi, rc, prec, accumulate_into=None):
+    rs = se.RealSpace(len(q), L, xi, rc, precision=prec)
+    dt = rs.dtype
+    xd = torch.as_tensor(np.asarray(x), dtype=dt).cuda().contiguous()
+    qd = torch.as_tensor(np.asarray(q), dtype=dt).cuda().contiguous()
+    F = torch.empty((len(q), 3), dtype=dt, device="cuda")
+    phi = torch.empty(len(q), dtype=dt, device="cuda")
+    E = torch.zeros(1, dtype=torch.float64, device="cuda")
+    rs.evaluate(xd, qd, F, phi, E)
+    torch.cuda.synchronize()
+    out = dict(F=F.double().cpu().numpy(), phi=phi.double().cpu().numpy(), E=E.item(),
+               cells=rs.cells_per_dim())
+    rs.close()
+    return out
+
+
+def _clustered(L, n_cluster, n_rest, seed):
+    """A dense cluster in one corner cell (more particles than the staged
+    neighbourhood holds) plus a sparse rest.  The cluster's charges share one
+    sign (0.5 to 1): alternating charges that close together would cancel
+    terms of ~60 down to sums of order 1, and single-precision rounding would
+    measure the cancellation, not the kernel."""
+    rng = np.random.default_rng(seed)
+    xc = 0.05 + 0.25 * rng.random((n_cluster, 3))
+    xr = L * rng.random((n_rest, 3))
+    x = np.vstack([xc, xr])
+    q = np.concatenate([0.5 + 0.5 * rng.random(n_cluster),
+                        np.where(np.arange(n_rest) % 2 == 0, 1.0, -1.0)])
+    return x, q
+
+
+CASES = [  # (name, L, xi, rc): three cells per dimension (rc = L/3), six, a small rc
+    ("uniform", 3.0, 3.5, 1.0), ("uniform", 3.0, 3.5, 0.5), ("uniform", 2.0, 5.0, 0.3),
+    ("clustered", 3.0, 3.5, 0.9), ("water", 2.0, 3.12, 0.6)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name,L,xi,rc", CASES)
+def test_real_space_parity(prec, name, L, xi, rc):
+    if name == "uniform":
+        x, q = systems.uniform_charges(900, L, seed=int(rc * 100))
+    elif name == "clustered":
+        x, q = _clustered(L, 5000 if prec == "fp32" else 2500, 300, seed=7)
+    else:
+        x, q = systems.water_box(L, seed=5)
+    g = run_real(x, q, L, xi, rc, prec)
+    assert g["cells"] == min(40, int(math.floor(L / rc)))
+    r = oracle.ewald_real(x, q, L, xi, rc)
+    phi_o = r["phi_real"] + r["phi_self"]
+    assert rel(g["phi"], phi_o) < TOL[prec]
+    assert rel(g["F"], r["F_real"]) < TOL[prec]
+    E_o = r["E_real"] + r["E_self"]
+    assert abs(g["E"] - E_o) < max(TOL[prec], 1e-13) * abs(E_o) * (10 if prec == "fp32" else 1)
+
+
+def test_full_ewald_with_selected_parameters():
+    """k-space plan (FP64) plus real space accumulated into the same outputs:
+    within 2 tol of the converged Ewald total at parameters chosen by
+    se_select_params for an rms force tolerance."""
+    L, tol, rc = 2.0, 1e-6, 0.6
+    x, q = systems.uniform_charges(400, L, seed=17)
+    Q = float((q ** 2).sum())
+    s = se.select_params("force", tol, rc, L, Q)
+    plan = se.Plan(len(q), L, s["xi"], s["M"], s["P"], precision="fp64")
+    rs = se.RealSpace(len(q), L, s["xi"], rc, precision="fp64")
+    xd = torch.as_tensor(x, dtype=torch.float64).cuda().contiguous()
+    qd = torch.as_tensor(q, dtype=torch.float64).cuda().contiguous()
+    F = torch.empty((len(q), 3), dtype=torch.float64, device="cuda")
+    phi = torch.empty(len(q), dtype=torch.float64, device="cuda")
+    E = torch.zeros(1, dtype=torch.float64, device="cuda")
+    plan.evaluate(xd, qd, F, phi, E)
+    rs.evaluate(xd, qd, F, phi, E, accumulate=True)
+    torch.cuda.synchronize()
+    E_t, phi_t, F_t = oracle.ewald_total(x, q, L, s["xi"])
+    err = math.sqrt(((F.cpu().numpy() - F_t) ** 2).sum(1).mean())
+    assert err <= 2 * tol, (s, err)
+    assert abs(E.item() - E_t) < 1e-3 * abs(E_t)
+    assert rel(phi.cpu().numpy(), phi_t) < 1e-4
+    plan.close()
+    rs.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_real_space_water_box_sampled(prec):
+    """The 21 642-atom water box (L = 6 nm, xi = 3.12, rc = 1 nm): the GPU
+    potential and force at 48 sampled atoms against the oracle's image sum at
+    those atoms; the energy identity E = 1/2 sum q phi on the whole box."""
+    L, xi, rc = 6.0, 3.12, 1.0
+    x, q = systems.water_box(L, seed=2)
+    g = run_real(x, q, L, xi, rc, prec)
+    idx = np.random.default_rng(3).choice(len(q), 48, replace=False)
+    ph_o, F_o = oracle.ewald_real_at(x, q, L, xi, rc, idx)
+    ph_o = ph_o - 2.0 * xi / math.sqrt(math.pi) * q[idx]
+    assert rel(g["phi"][idx], ph_o) < TOL[prec]
+    assert rel(g["F"][idx], F_o) < TOL[prec]
+    assert abs(g["E"] - 0.5 * (q * g["phi"]).sum()) < 1e-6 * abs(g["E"])
+
+
+def test_real_space_accumulate_and_empty():
+    L, xi, rc = 3.0, 3.5, 1.0
+    x, q = systems.uniform_charges(500, L, seed=2)
+    rs = se.RealSpace(len(q), L, xi, rc)
+    xd = torch.as_tensor(x).cuda().contiguous()
+    qd = torch.as_tensor(q).cuda().contiguous()
+    F = torch.ones((len(q), 3), dtype=torch.float64, device="cuda")
+    phi = torch.full((len(q),), 2.0, dtype=torch.float64, device="cuda")
+    E = torch.full((1,), 5.0, dtype=torch.float64, device="cuda")
+    rs.evaluate(xd, qd, F, phi, E, accumulate=True)
+    torch.cuda.synchronize()
+    r = oracle.ewald_real(x, q, L, xi, rc)
+    assert rel(F.cpu().numpy() - 1.0, r["F_real"]) < 1e-12
+    assert rel(phi.cpu().numpy() - 2.0, r["phi_real"] + r["phi_self"]) < 1e-12
+    assert abs(E.item() - 5.0 - (r["E_real"] + r["E_self"])) < 1e-11 * abs(r["E_real"])
+    rs.close()
+    empty = se.RealSpace(0, L, xi, rc)
+    E0 = torch.full((1,), 3.0, dtype=torch.float64, device="cuda")
+    empty.evaluate(None, None, None, None, E0)
+    torch.cuda.synchronize()
+    assert E0.item() == 0.0
+    empty.close()
