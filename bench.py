@@ -408,6 +408,7 @@ def run_ours(args):
             out["unsorted_variant"] = unsorted_variant(se, torch, x, q, w, prec, min(K, 1000), flush)
         out["autograd"] = autograd_timing(se, torch, x, q, w, prec, max(20, min(K, 500)), flush)
         out["modes"] = other_modes(se, torch, x, q, w, prec, min(K, 500), flush, (variant, tile))
+        out["real_space"] = real_space(se, torch, x, q, w, prec, min(K, 500), flush, plan)
         out["cpu_baseline"] = cpu_baseline(x, q, w, args.cpu_seconds)
     plan.close()
     if ws > 1:
@@ -690,6 +691,42 @@ def other_modes(se, torch, x, q, w, prec, K, flush, cfg):
             r["rel_rms_force_err"] = rel_rms(F.double().cpu().numpy(), Fref)
         out[mode] = r
         plan.close()
+    return out
+
+
+def real_space(se, torch, x, q, w, prec, K, flush, plan):
+    """The real-space part of the Ewald sum (cell lists, cut-off 1 nm, or L/3
+    for boxes under 3 nm) on the same input, alone and after the k-space
+    evaluation into the same outputs (the whole Ewald sum)."""
+    N = len(q)
+    rc = min(1.0, w["L"] / 3.0)
+    rprec = "fp64" if prec == "fp64" else "fp32"
+    rs = se.RealSpace(N, w["L"], w["xi"], rc, precision=rprec)
+    dt = rs.dtype
+    xd = torch.tensor(x, dtype=dt, device="cuda")
+    qd = torch.tensor(q, dtype=dt, device="cuda")
+    F = torch.empty((N, 3), dtype=dt, device="cuda")
+    phi = torch.empty((N,), dtype=dt, device="cuda")
+    Ed = torch.zeros(1, dtype=torch.float64, device="cuda")
+    out = {"rc": rc, "cells_per_dim": rs.cells_per_dim(), "precision": rprec}
+    for key, both in (("real_only", False), ("whole_ewald", True)):
+        def step():
+            if both:
+                plan.evaluate(xd, qd, F, phi, Ed)
+            rs.evaluate(xd, qd, F, phi, Ed, accumulate=both)
+        for _ in range(10):
+            step()
+        st = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        en = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        for i in range(K):
+            flush()
+            st[i].record()
+            step()
+            en[i].record()
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in zip(st, en)) / K
+        out[key] = {"value": 1e3 / ms, "unit": "evals/s", "ms_per_step": ms, "steps": K}
+    rs.close()
     return out
 
 

@@ -275,8 +275,10 @@ int se_spread_noalloc(const double *xyz, const double *q, int64_t N, double L, d
  *           (x_m - x_n)/r^2            (the image of x_n at distance r)
  *   E     = 1/2 sum q_m phi_m  (real-space energy plus the self energy)
  * Added to se_evaluate's k-space results they give the whole Ewald potential,
- * force and energy.  Cells of edge >= rc (L/rc per dimension, at most 40) hold
- * the particles; rc > L/3 returns SE_ERR_UNSUPPORTED at creation.
+ * force and energy.  Cells of edge >= rc/K hold the particles (K L/rc per
+ * dimension, at most 40; K = 2, or 3 for more than 24 particles per K = 2
+ * cell; se_real_get_cells reports the count);
+ * rc > L/3 returns SE_ERR_UNSUPPORTED at creation.
  * se_real_evaluate: xyz [N][3], q [N], F [N][3], phi [N] DEVICE arrays of the
  * precision's type (SE_FP64 double, SE_FP32 float), E a DEVICE double; F,
  * phi and E may be NULL.  accumulate = 0 overwrites the outputs, 1 adds to

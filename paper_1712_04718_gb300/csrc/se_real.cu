@@ -11,14 +11,16 @@
 // so that these plus the k-space results of se_evaluate are the whole Ewald
 // potential, force and energy.
 //
-// GPU design: particles are counted into cells of edge >= r_c (nc = floor(L
-// / r_c) per dimension, nc >= 3, so the 27 neighbour cells of a cell are 27
-// distinct periodic images and every pair within r_c is met exactly once),
-// scanned and scattered into cell order.  One CTA per home cell stages the
-// 27 neighbour cells in shared memory with their image shift applied (in
-// chunks when they do not fit), and each home particle's candidate loop is
-// split over S adjacent lanes (S a power of two, S x home particles <= the
-// CTA), reduced by shuffles.  Every particle sums its own potential and
+// GPU design: particles are counted into cells of edge >= r_c / K (nc =
+// floor(K L / r_c) per dimension, at most 40, nc >= 2K+1, so the (2K+1)^3
+// cells around a cell are distinct periodic images and every pair within r_c
+// is met exactly once), scanned and scattered into cell order.  One CTA per
+// home cell stages its stencil in shared memory with the image shifts
+// applied (the cells' ranges fetched in parallel, offsets by a warp scan,
+// each staged particle located by binary search; in chunks when they do not
+// fit), and each home particle's candidate loop is split over S adjacent
+// lanes (S a power of two, S x home particles <= the CTA), reduced by
+// shuffles.  Every particle sums its own potential and
 // force: no atomics on the outputs.  The energy is a deterministic two-level
 // reduction (last block).
 #include <cuda_runtime.h>
@@ -36,7 +38,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kMaxCellsPerDim = 40;     // at most 64 000 cells (one energy partial each)
-constexpr size_t kNbSmem = 64 * 1024;   // shared memory for staged neighbours
+constexpr size_t kNbSmem = 32 * 1024;   // shared memory for staged neighbours
 
 template <typename T> struct R4 { using type = se::v4_t<T>; };
 
@@ -155,20 +157,61 @@ __device__ __forceinline__ double block_sum_d(double v, double* sbuf) {
     return r;
 }
 
+// Stencil of a home cell: the (2K+1)^3 cells within K cells per direction
+// (cells of edge >= rc / K, so that every pair within rc has both ends in
+// such a pair of cells), each a distinct periodic image since nc >= 2K+1.
+constexpr int kMaxStencil = 343;   // K <= 3
+constexpr int kPairThreads = 128;
+
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kPairThreads)
 k_rs_pairs(const typename R4<T>::type* __restrict__ sorted, const int* __restrict__ start,
-           const int* __restrict__ perm, int nc, T L, T rc2, T xi, T c2xi, T kc, int cap,
+           const int* __restrict__ perm, int nc, int K, T L, T rc2, T xi, T c2xi, T kc, int cap,
            T* __restrict__ phi, T* __restrict__ F, int accumulate, double* __restrict__ partials,
            unsigned* ticket, double* E_out) {
     using V = typename R4<T>::type;
     extern __shared__ __align__(32) unsigned char smem_raw[];
     V* nb = reinterpret_cast<V*>(smem_raw);
+    __shared__ int s_b0[kMaxStencil], s_off[kMaxStencil + 1];
+    __shared__ unsigned char s_sh[kMaxStencil];   // image shift per axis: 0, 1 (-L), 2 (+L)
     __shared__ double sbuf[32];
     __shared__ bool last;
     const int cid = blockIdx.x;
     const int cx = cid / (nc * nc), cy = (cid / nc) % nc, cz = cid % nc;
     const int h0 = start[cid], nh = start[cid + 1] - h0;
+    const int W = 2 * K + 1, W3 = W * W * W;
+    // the stencil's cells: range and image shift, then offsets by a one-warp scan
+    for (int k = threadIdx.x; k < W3; k += blockDim.x) {
+        int nx = cx + k / (W * W) - K, ny = cy + (k / W) % W - K, nz = cz + k % W - K;
+        unsigned char sh = 0;
+        if (nx < 0) { nx += nc; sh |= 1; } else if (nx >= nc) { nx -= nc; sh |= 2; }
+        if (ny < 0) { ny += nc; sh |= 4; } else if (ny >= nc) { ny -= nc; sh |= 8; }
+        if (nz < 0) { nz += nc; sh |= 16; } else if (nz >= nc) { nz -= nc; sh |= 32; }
+        const int nid = (nx * nc + ny) * nc + nz;
+        const int b0 = start[nid];
+        s_b0[k] = b0;
+        s_off[k + 1] = start[nid + 1] - b0;   // count, scanned below
+        s_sh[k] = sh;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        int carry = 0;
+        if (lane == 0) s_off[0] = 0;
+        for (int base = 0; base < W3; base += 32) {
+            const int k = base + lane;
+            int v = k < W3 ? s_off[k + 1] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
+            }
+            if (k < W3) s_off[k + 1] = carry + v;
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
+    }
+    __syncthreads();
+    const int total = s_off[W3];
     int S = 1;
     while (S < 32 && 2 * S * nh <= (int)blockDim.x) S <<= 1;
     const int per_pass = blockDim.x / S;
@@ -181,34 +224,22 @@ k_rs_pairs(const typename R4<T>::type* __restrict__ sorted, const int* __restric
         me.x = me.y = me.z = me.w = T(0);
         if (act) me = sorted[h0 + li];
         T ph = T(0), fx = T(0), fy = T(0), fz = T(0);
-        // stream the 27 neighbour cells through shared memory, cap at a time
-        int k = 0, koff = 0;
-        while (k < 27) {
-            int filled = 0;
+        for (int c0 = 0; c0 < total; c0 += cap) {
+            const int filled = min(cap, total - c0);
             __syncthreads();
-            while (k < 27 && filled < cap) {
-                const int dx = k / 9 - 1, dy = (k / 3) % 3 - 1, dz = k % 3 - 1;
-                int nx = cx + dx, ny = cy + dy, nz = cz + dz;
-                T sx = T(0), sy = T(0), sz = T(0);
-                if (nx < 0) { nx += nc; sx = -L; } else if (nx >= nc) { nx -= nc; sx = L; }
-                if (ny < 0) { ny += nc; sy = -L; } else if (ny >= nc) { ny -= nc; sy = L; }
-                if (nz < 0) { nz += nc; sz = -L; } else if (nz >= nc) { nz -= nc; sz = L; }
-                const int nid = (nx * nc + ny) * nc + nz;
-                const int b0 = start[nid], cnt = start[nid + 1] - b0;
-                const int take = min(cnt - koff, cap - filled);
-                for (int t = threadIdx.x; t < take; t += blockDim.x) {
-                    V v = sorted[b0 + koff + t];
-                    v.x += sx;
-                    v.y += sy;
-                    v.z += sz;
-                    nb[filled + t] = v;
+            for (int t = threadIdx.x; t < filled; t += blockDim.x) {
+                const int g = c0 + t;
+                int lo = 0, hi = W3 - 1;   // the cell k with s_off[k] <= g < s_off[k + 1]
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_off[mid] <= g) lo = mid; else hi = mid - 1;
                 }
-                filled += take;
-                koff += take;
-                if (koff == cnt) {
-                    ++k;
-                    koff = 0;
-                }
+                V v = sorted[s_b0[lo] + g - s_off[lo]];
+                const unsigned sh = s_sh[lo];
+                v.x += (sh & 1) ? -L : ((sh & 2) ? L : T(0));
+                v.y += (sh & 4) ? -L : ((sh & 8) ? L : T(0));
+                v.z += (sh & 16) ? -L : ((sh & 32) ? L : T(0));
+                nb[t] = v;
             }
             __syncthreads();
             if (act) {
@@ -297,7 +328,7 @@ struct se_real {
     double L = 0, xi = 0, rc = 0, kc = 1.0;
     int prec = SE_FP64;
     cudaStream_t stream = nullptr;
-    int nc = 0, ncells = 0;
+    int nc = 0, ncells = 0, K = 1;   // cells per dimension, stencil reach
     bool ready = false;
     int ready_prec = -1;
     int* count = nullptr;
@@ -369,8 +400,8 @@ int rs_run(se_real* r, const void* xyz, const void* q, void* F, void* phi, doubl
                              (int)kNbSmem) != cudaSuccess)
         return SE_ERR_CUDA;
     const double c2xi = 2.0 * r->xi / sqrt(3.14159265358979323846);
-    k_rs_pairs<T><<<r->ncells, kThreads, kNbSmem, s>>>(
-        (const V*)r->sorted, r->start, r->perm, nc, L, (T)(r->rc * r->rc), (T)r->xi, (T)c2xi,
+    k_rs_pairs<T><<<r->ncells, kPairThreads, kNbSmem, s>>>(
+        (const V*)r->sorted, r->start, r->perm, nc, r->K, L, (T)(r->rc * r->rc), (T)r->xi, (T)c2xi,
         (T)r->kc, cap, (T*)phi, (T*)F, acc, r->partials, r->ticket, E);
     return cudaGetLastError() == cudaSuccess ? SE_OK : SE_ERR_CUDA;
 }
@@ -383,15 +414,26 @@ extern "C" int se_real_create(se_real** out, int64_t N, double L, double xi, dou
     if (N < 0 || N >= ((int64_t)1 << 31) || !(L > 0.0) || !isfinite(L) || !(xi > 0.0) ||
         !isfinite(xi) || !(rc > 0.0) || !isfinite(rc))
         return SE_ERR_ARG;
-    const double cells = floor(L / rc);
-    if (cells < 3.0) return SE_ERR_UNSUPPORTED;   // r_c > L/3
+    if (floor(L / rc) < 3.0) return SE_ERR_UNSUPPORTED;   // r_c > L/3
+    // stencil reach K: cells of edge >= rc/K, nc >= 2K+1 distinct images
+    // (rc <= L/3 gives floor(2 L / rc) >= 6); K = 2 by default (a 5^3 stencil:
+    // fewer candidates per particle than 3^3 cells of edge rc, and 8 times
+    // the CTAs), K = 3 for dense boxes (more than 24 particles per K = 2 cell)
+    auto cells_for = [&](int K) {
+        return (int)std::min<double>(floor(K * L / rc), kMaxCellsPerDim);
+    };
+    int K = 2;
+    if (cells_for(3) >= 7 &&
+        (double)N / ((double)cells_for(2) * cells_for(2) * cells_for(2)) > 24.0)
+        K = 3;
     se_real* r = new (std::nothrow) se_real;
     if (!r) return SE_ERR_NOMEM;
     r->N = N;
     r->L = L;
     r->xi = xi;
     r->rc = rc;
-    r->nc = (int)std::min<double>(cells, kMaxCellsPerDim);
+    r->K = K;
+    r->nc = cells_for(K);
     r->ncells = r->nc * r->nc * r->nc;
     *out = r;
     return SE_OK;
