@@ -276,8 +276,8 @@ int se_spread_noalloc(const double *xyz, const double *q, int64_t N, double L, d
  *   E     = 1/2 sum q_m phi_m  (real-space energy plus the self energy)
  * Added to se_evaluate's k-space results they give the whole Ewald potential,
  * force and energy.  Cells of edge >= rc/K hold the particles (K L/rc per
- * dimension, at most 40; K = 2, or 3 for more than 24 particles per K = 2
- * cell; se_real_get_cells reports the count);
+ * dimension, at most 40; K = 2, or 3 when K = 2 gives fewer than 512 cells;
+ * se_real_get_cells reports the count, se_real_set_reach overrides K);
  * rc > L/3 returns SE_ERR_UNSUPPORTED at creation.
  * se_real_evaluate: xyz [N][3], q [N], F [N][3], phi [N] DEVICE arrays of the
  * precision's type (SE_FP64 double, SE_FP32 float), E a DEVICE double; F,
@@ -292,6 +292,10 @@ int se_real_set_precision(se_real *real, int prec);   /* SE_FP64 (default) or SE
 int se_real_set_prefactor(se_real *real, double kc);
 int se_real_set_stream(se_real *real, void *stream);
 int se_real_get_cells(const se_real *real, int *cells_per_dim);
+/* Stencil reach K (cells of edge >= rc/K, a (2K+1)^3 stencil): 1, 2 or 3, or
+ * 0 for the automatic choice; SE_ERR_UNSUPPORTED if 2K+1 cells do not fit in
+ * L (at most 40 cells per dimension). */
+int se_real_set_reach(se_real *real, int K);
 int se_real_evaluate(se_real *real, const void *xyz, const void *q, void *F, void *phi,
                      double *E, int accumulate);
 

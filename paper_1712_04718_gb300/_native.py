@@ -76,6 +76,7 @@ SIGNATURES = {
     "se_real_set_prefactor": (_i, [_vp, _d]),
     "se_real_set_stream": (_i, [_vp, _vp]),
     "se_real_get_cells": (_i, [_vp, ctypes.POINTER(_i)]),
+    "se_real_set_reach": (_i, [_vp, _i]),
     "se_real_evaluate": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i]),
     "se_select_params": (_i, [_i, _d, _d, _d, _d, _d, _dp, ctypes.POINTER(_i),
                               ctypes.POINTER(_i), _dp]),

@@ -42,12 +42,49 @@ constexpr size_t kNbSmem = 32 * 1024;   // shared memory for staged neighbours
 
 template <typename T> struct R4 { using type = se::v4_t<T>; };
 
-__device__ __forceinline__ float erfcT(float a) { return erfcf(a); }
-__device__ __forceinline__ double erfcT(double a) { return erfc(a); }
-__device__ __forceinline__ float expR(float a) { return expf(a); }
-__device__ __forceinline__ double expR(double a) { return exp(a); }
-__device__ __forceinline__ float sqrtR(float a) { return sqrtf(a); }
-__device__ __forceinline__ double sqrtR(double a) { return sqrt(a); }
+// Single precision: erfc(x) = erfcx(x) e^{-x^2} with erfcx(x) ~ t P(t),
+// t = 1 / (1 + p x), P of degree 8 (the form of Hastings' approximations,
+// Abramowitz and Stegun 7.1.26), coefficients fitted by gen_erfcx_fit.py for
+// relative accuracy on 0 <= x <= 6 (3.5e-7 evaluated in float32; beyond 6,
+// where erfc < 2e-17, within 2e-5).  The e^{-x^2} is the one the force term
+// needs anyway, so each pair evaluates one exponential.
+constexpr float kErfcxP = 4.50000000e-01f;
+__constant__ float kErfcx[9] = {
+    2.536794543e-01f,
+    2.576121688e-01f,
+    1.990700811e-01f,
+    3.049189448e-01f,
+    -2.398110330e-01f,
+    6.246721148e-01f,
+    -6.125214100e-01f,
+    2.510224283e-01f,
+    -3.864272311e-02f};
+
+__device__ __forceinline__ float erfcx_fit(float x) {
+    const float t = __fdividef(1.0f, fmaf(kErfcxP, x, 1.0f));   // 2 ulp
+    float a = kErfcx[8];
+#pragma unroll
+    for (int k = 7; k >= 0; --k) a = fmaf(a, t, kErfcx[k]);
+    return a * t;
+}
+
+// erfc(xi r)/r and the force factor (2 xi/sqrt(pi) e^{-xi^2 r^2} + erfc(xi r)/r)/r^2
+// for one pair, given r^2 and 1/r.
+__device__ __forceinline__ void pair_terms(float r2, float ir, float xi, float c2xi, float& ec,
+                                           float& fr) {
+    const float x = xi * (r2 * ir);
+    const float e = expf(-x * x);
+    ec = erfcx_fit(x) * e * ir;
+    fr = (c2xi * e + ec) * ir * ir;
+}
+__device__ __forceinline__ void pair_terms(double r2, double ir, double xi, double c2xi,
+                                           double& ec, double& fr) {
+    const double r = r2 * ir;
+    ec = erfc(xi * r) * ir;
+    fr = (c2xi * exp(-xi * xi * r2) + ec) * ir * ir;
+}
+__device__ __forceinline__ float rsqrtR(float a) { return rsqrtf(a); }
+__device__ __forceinline__ double rsqrtR(double a) { return rsqrt(a); }
 __device__ __forceinline__ float floorR(float a) { return floorf(a); }
 __device__ __forceinline__ double floorR(double a) { return floor(a); }
 
@@ -264,11 +301,10 @@ k_rs_pairs(const typename R4<T>::type* __restrict__ sorted, const int* __restric
                         const V n = nb[j0 + b * S];
                         const T dx = me.x - n.x, dy = me.y - n.y, dz = me.z - n.z;
                         const T r2 = dx * dx + dy * dy + dz * dz;
-                        const T r = sqrtR(r2);
-                        const T ir = T(1) / r;
-                        const T ec = erfcT(xi * r) * ir;
+                        T ec, fr;
+                        pair_terms(r2, rsqrtR(r2), xi, c2xi, ec, fr);
                         ph += n.w * ec;
-                        const T f = n.w * (c2xi * expR(-xi * xi * r2) + ec) * ir * ir;
+                        const T f = n.w * fr;
                         fx += f * dx;
                         fy += f * dy;
                         fz += f * dz;
@@ -408,24 +444,40 @@ int rs_run(se_real* r, const void* xyz, const void* q, void* F, void* phi, doubl
 
 }  // namespace
 
+// Cells per dimension and stencil reach for (N, L, rc); reach_user 1-3
+// forces K (SE_ERR_UNSUPPORTED if its 2K+1 cells do not fit), 0 chooses.
+static int rs_layout(int64_t N, double L, double rc, int reach_user, int* K_out, int* nc_out) {
+    if (floor(L / rc) < 3.0) return SE_ERR_UNSUPPORTED;   // r_c > L/3
+    // stencil reach K: cells of edge >= rc/K, nc >= 2K+1 distinct images
+    // (rc <= L/3 gives floor(2 L / rc) >= 6); K = 2 by default (a 5^3 stencil:
+    // fewer candidates per particle than 3^3 cells of edge rc, and 8 times
+    // the CTAs; measured 2-5 times faster than K = 1 and 1.2-1.5 times faster
+    // than K = 3 on water boxes of 21.6k and 100k atoms), K = 3 when K = 2
+    // leaves fewer than 512 cells (CTAs) for the GPU (1000 charges in a 3 nm
+    // box: 1.3 times faster than K = 2)
+    auto cells_for = [&](int K) {
+        return (int)std::min<double>(floor(K * L / rc), kMaxCellsPerDim);
+    };
+    (void)N;
+    int K = 2;
+    if (reach_user >= 1) K = reach_user;
+    else if (cells_for(3) >= 7 && cells_for(2) * cells_for(2) * cells_for(2) < 512)
+        K = 3;
+    if (cells_for(K) < 2 * K + 1) return SE_ERR_UNSUPPORTED;
+    *K_out = K;
+    *nc_out = cells_for(K);
+    return SE_OK;
+}
+
 extern "C" int se_real_create(se_real** out, int64_t N, double L, double xi, double rc) {
     if (!out) return SE_ERR_ARG;
     *out = nullptr;
     if (N < 0 || N >= ((int64_t)1 << 31) || !(L > 0.0) || !isfinite(L) || !(xi > 0.0) ||
         !isfinite(xi) || !(rc > 0.0) || !isfinite(rc))
         return SE_ERR_ARG;
-    if (floor(L / rc) < 3.0) return SE_ERR_UNSUPPORTED;   // r_c > L/3
-    // stencil reach K: cells of edge >= rc/K, nc >= 2K+1 distinct images
-    // (rc <= L/3 gives floor(2 L / rc) >= 6); K = 2 by default (a 5^3 stencil:
-    // fewer candidates per particle than 3^3 cells of edge rc, and 8 times
-    // the CTAs), K = 3 for dense boxes (more than 24 particles per K = 2 cell)
-    auto cells_for = [&](int K) {
-        return (int)std::min<double>(floor(K * L / rc), kMaxCellsPerDim);
-    };
-    int K = 2;
-    if (cells_for(3) >= 7 &&
-        (double)N / ((double)cells_for(2) * cells_for(2) * cells_for(2)) > 24.0)
-        K = 3;
+    int K = 0, nc = 0;
+    const int st = rs_layout(N, L, rc, 0, &K, &nc);
+    if (st != SE_OK) return st;
     se_real* r = new (std::nothrow) se_real;
     if (!r) return SE_ERR_NOMEM;
     r->N = N;
@@ -433,9 +485,21 @@ extern "C" int se_real_create(se_real** out, int64_t N, double L, double xi, dou
     r->xi = xi;
     r->rc = rc;
     r->K = K;
-    r->nc = cells_for(K);
-    r->ncells = r->nc * r->nc * r->nc;
+    r->nc = nc;
+    r->ncells = nc * nc * nc;
     *out = r;
+    return SE_OK;
+}
+
+extern "C" int se_real_set_reach(se_real* r, int K) {
+    if (!r || K < 0 || K > 3) return SE_ERR_ARG;
+    int Kn = 0, nc = 0;
+    const int st = rs_layout(r->N, r->L, r->rc, K, &Kn, &nc);
+    if (st != SE_OK) return st;
+    if (nc * nc * nc != r->ncells) rs_release(r);   // buffers sized by the cell count
+    r->K = Kn;
+    r->nc = nc;
+    r->ncells = nc * nc * nc;
     return SE_OK;
 }
 

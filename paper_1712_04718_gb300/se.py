@@ -279,6 +279,10 @@ class RealSpace:
     def dtype(self):
         return _TORCH_DTYPE[self.prec]
 
+    def set_reach(self, K):
+        """Stencil reach 1-3 (cells of edge >= rc/K), 0 automatic."""
+        nat.check(self._lib.se_real_set_reach(self._h, int(K)), "se_real_set_reach")
+
     def cells_per_dim(self):
         n = ctypes.c_int()
         nat.check(self._lib.se_real_get_cells(self._h, ctypes.byref(n)), "se_real_get_cells")

@@ -84,8 +84,8 @@ def test_argument_validation(lib):
 
 def test_real_space_arguments(lib):
     """se_real_create validates its arguments on the host; the cell grid is
-    floor(K L / rc) per dimension (K = 2 here), at most 40; rc > L/3 is not
-    supported."""
+    floor(K L / rc) per dimension (K = 2, or 3 when K = 2 gives under 512
+    cells), at most 40; rc > L/3 is not supported."""
     from paper_1712_04718_gb300 import _native as nat
     h = ctypes.c_void_p()
     for args in ((-1, 3.0, 3.0, 1.0), (10, 0.0, 3.0, 1.0), (10, 3.0, -1.0, 1.0),
@@ -93,9 +93,14 @@ def test_real_space_arguments(lib):
         assert lib.se_real_create(ctypes.byref(h), *args) == nat.SE_ERR_ARG, args
     assert lib.se_real_create(ctypes.byref(h), 10, 3.0, 3.0, 1.01) == nat.SE_ERR_UNSUPPORTED
     n = ctypes.c_int()
-    for L, rc, cells in ((3.0, 1.0, 6), (6.0, 1.0, 12), (10.0, 0.9, 22), (100.0, 1.0, 40)):
+    for L, rc, cells in ((3.0, 1.0, 9), (6.0, 1.0, 12), (10.0, 0.9, 22), (100.0, 1.0, 40)):
         assert lib.se_real_create(ctypes.byref(h), 10, L, 3.0, rc) == nat.SE_OK
         assert lib.se_real_get_cells(h, ctypes.byref(n)) == nat.SE_OK and n.value == cells
+        assert lib.se_real_set_reach(h, 4) == nat.SE_ERR_ARG
+        assert lib.se_real_set_reach(h, 1) == nat.SE_OK
+        assert lib.se_real_get_cells(h, ctypes.byref(n)) == nat.SE_OK
+        assert n.value == min(40, int(L / rc))
+        assert lib.se_real_set_reach(h, 0) == nat.SE_OK
         assert lib.se_real_set_precision(h, 5) == nat.SE_ERR_ARG
         assert lib.se_real_set_prefactor(h, -1.0) == nat.SE_ERR_ARG
         assert lib.se_real_destroy(h) == nat.SE_OK
