@@ -205,6 +205,30 @@ def kernel_sources_sha():
     return h.hexdigest()[:16]
 
 
+def cost_model(stages, nstage, N, M, P, variant):
+    """The paper's cost model T = c_sp-ga N P^3 + c_fft (M^3/2) log2(M^3/2) +
+    c_solve M^3 (Sec. 6.2) with its constants taken from this run's per-stage
+    times (direct launches): spread, gather and bin against N P^3, the
+    transforms against (M^3/2) log2(M^3/2), the scaling against M^3 (in the
+    single-precision pipeline the scaling pass also holds the x transforms).
+    The paper's values for one i7-3770 core in FP64 are given beside them."""
+    n = max(1, nstage)
+    us = {k: v / n * 1e3 for k, v in stages.items()}
+    m3 = float(M) ** 3
+    fft_units = (m3 / 2.0) * math.log2(m3 / 2.0)
+    return {
+        "c_spread_gather_s": (us["bin"] + us["scatter"] + us["spread"] + us["gather"]) * 1e-6 /
+                             (float(N) * P ** 3),
+        "c_fft_s": (us["fft_fwd"] + us["fft_inv"]) * 1e-6 / fft_units,
+        "c_solve_s": us["scale"] * 1e-6 / m3,
+        "note": "per-stage CUDA events around single launches (launch latency included); "
+                "scaling pass includes the x transforms" if variant in (3, 4) else
+                "per-stage CUDA events around single launches (launch latency included)",
+        "paper_i7_3770_1core_fp64": {"c_spread_gather_s": 5e-9, "c_fft_s": 4.5e-9,
+                                     "c_solve_s": 2e-9},
+    }
+
+
 def profiled_traffic(kernel, workload_name):
     """DRAM bytes per launch (read + write) of `kernel` on `workload_name` from
     a committed ncu summary profiles/ncu_<name>_<workload>.md: a line
@@ -389,6 +413,7 @@ def run_ours(args):
         "stages_note": "per-stage CUDA events, direct launches, %d evaluations (the headline "
                        "replays one CUDA graph per evaluation)" % nstage,
         "fft_us_per_eval": (stages["fft_fwd"] + stages["fft_inv"]) / max(1, nstage) * 1e3,
+        "cost_model": cost_model(stages, nstage, N, w["M"], w["P"], variant),
         "roofline": roof,
         "gpu_launches": {3: 6, 4: 5}.get(variant, 5) * K,
         "gpu_launches_note": {
