@@ -716,6 +716,16 @@ def other_modes(se, torch, x, q, w, prec, K, flush, cfg):
             r["rel_rms_force_err"] = rel_rms(F.double().cpu().numpy(), Fref)
         out[mode] = r
         plan.close()
+    # the ik oracle once on the whole workload (small workloads only)
+    if w["M"] <= 64:
+        import oracle
+        t0 = time.perf_counter()
+        oracle.se_kspace_ik(np.asarray(x, np.float64), np.asarray(q, np.float64), w["L"],
+                            w["xi"], w["M"], w["P"])
+        dt = time.perf_counter() - t0
+        out["ik_forces"]["cpu_baseline"] = {"value": 1.0 / dt, "unit": "evals/s",
+                                            "cores": oracle.num_threads(), "kind": "oracle",
+                                            "sample": "one whole evaluation"}
     return out
 
 
@@ -734,6 +744,14 @@ def real_space(se, torch, x, q, w, prec, K, flush, plan):
     phi = torch.empty((N,), dtype=dt, device="cuda")
     Ed = torch.zeros(1, dtype=torch.float64, device="cuda")
     out = {"rc": rc, "cells_per_dim": rs.cells_per_dim(), "precision": rprec}
+    # algorithmic work: (2K+1)^3 (rc/K)^3 rho distance tests (8 flops) and
+    # (4 pi/3) rc^3 rho pair terms (about 40 flops with the transcendentals)
+    nc = rs.cells_per_dim()
+    K = max(1, int(round(nc * rc / w["L"])))
+    rho = N / w["L"] ** 3
+    cand = (2 * K + 1) ** 3 * (w["L"] / nc) ** 3 * rho
+    hits = 4.0 / 3.0 * math.pi * rc ** 3 * rho
+    flops = N * (8.0 * cand + 40.0 * hits)
     for key, both in (("real_only", False), ("whole_ewald", True)):
         def step():
             if both:
@@ -751,7 +769,26 @@ def real_space(se, torch, x, q, w, prec, K, flush, plan):
         torch.cuda.synchronize()
         ms = sum(a.elapsed_time(b) for a, b in zip(st, en)) / K
         out[key] = {"value": 1e3 / ms, "unit": "evals/s", "ms_per_step": ms, "steps": K}
+    from paper_1712_04718_gb300 import se as _se
+    pk = _se.probe_peak("fp64_fma" if rprec == "fp64" else "fp32_fma") / 1e12
+    t = out["real_only"]["ms_per_step"] * 1e-3
+    out["roofline"] = {"kernel": "k_rs_pairs (+ count, scan, scatter)", "bound": "alu",
+                       "unit": "TFLOP/s", "achieved": flops / t / 1e12, "peak": pk,
+                       "frac": flops / t / 1e12 / pk,
+                       "work": "N (8 flops x %.0f candidates + 40 flops x %.0f pairs within rc)" % (cand, hits),
+                       "peak_source": "measured: se_probe_peak FMA rate (this run)"}
     rs.close()
+    # the oracle's real-space image sum at a sample of target atoms, scaled to the box
+    import oracle
+    ns = min(N, 64)
+    idx = np.random.default_rng(0).choice(N, ns, replace=False)
+    x64, q64 = np.asarray(x, np.float64), np.asarray(q, np.float64)
+    t0 = time.perf_counter()
+    oracle.ewald_real_at(x64, q64, w["L"], w["xi"], rc, idx)
+    dt = (time.perf_counter() - t0) * N / ns
+    out["cpu_baseline"] = {"value": 1.0 / dt, "unit": "evals/s", "cores": oracle.num_threads(),
+                           "kind": "oracle", "sample": "%d target atoms of the box (all images "
+                           "within rc), scaled to all %d" % (ns, N)}
     return out
 
 
