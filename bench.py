@@ -506,7 +506,50 @@ def run_ensemble(args, torch, se, ws, rank):
                    "spread_tile": tile, "l2": "flushed between steps (untimed)"},
         "gpu_launches": 8 * K, "clocks": clk,
     }
+    # per-stage times (direct launches with events between the stages) and the
+    # roofline of the dominant stage of spread and gather
+    b.set_timing(True)
+    for _ in range(20):
+        b.evaluate(xd, qd, F, phi, E)
+    torch.cuda.synchronize()
+    stages, nst = b.get_timing()
+    b.set_timing(False)
+    us = {k: v / max(1, nst) * 1e3 for k, v in stages.items()}
+    out["stages_us_per_eval"] = us
+    out["stages_note"] = "per-stage CUDA events, direct launches, %d evaluations" % nst
+    P3 = float(w["P"]) ** 3
+    if us["spread"] >= us["gather"]:
+        pk = se.probe_peak("smem_atomic_u32") / 1e9
+        ach = Ntot * P3 / (us["spread"] * 1e-6) / 1e9
+        out["roofline"] = {"kernel": "k_bspread", "bound": "alu", "unit": "Gop/s", "achieved": ach,
+                           "peak": pk, "frac": ach / pk, "traffic": None,
+                           "work": "N P^3 shared-memory atomic adds",
+                           "peak_source": "measured: se_probe_peak shared-memory u32 atomics"}
+    else:
+        pk = se.probe_peak("fp32_fma") / 1e12
+        ach = 4.0 * Ntot * P3 / (us["gather"] * 1e-6) / 1e12
+        out["roofline"] = {"kernel": "k_bgather_tile / k_bgather", "bound": "alu",
+                           "unit": "TFLOP/s", "achieved": ach, "peak": pk, "frac": ach / pk,
+                           "traffic": None, "work": "4 N P^3 flops",
+                           "peak_source": "measured: se_probe_peak FP32 FMA"}
     if rank == 0 and not args.no_extras:
+        # the FP64 oracle on whole systems of the ensemble, in order, until ~5 s
+        import oracle
+        t0 = time.perf_counter()
+        n_done = 0
+        k_sys = 0
+        for d in ens:
+            oracle.se_kspace(np.asarray(d["x"], np.float64), np.asarray(d["q"], np.float64),
+                             d["L"], w["xi"], d["M"], w["P"])
+            n_done += len(d["q"])
+            k_sys += 1
+            if time.perf_counter() - t0 > 5.0:
+                break
+        dt = (time.perf_counter() - t0) * Nall / n_done
+        out["cpu_baseline"] = {"value": 1.0 / dt, "unit": "ensemble evals/s",
+                               "cores": oracle.num_threads(), "kind": "oracle",
+                               "sample": "the first %d of %d systems (%d atoms), scaled by atoms"
+                                         % (k_sys, len(ens), n_done)}
         errs = []
         off = np.concatenate([[0], np.cumsum(Ns)])
         for s in range(0, len(mine), max(1, len(mine) // 4)):

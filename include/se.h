@@ -238,6 +238,14 @@ int se_batch_grid_energy(se_batch *batch, double *E_grid);
 /* Worst input check over the systems of the last evaluation (SE_OK,
  * SE_WARN_NONNEUTRAL or SE_ERR_NONFINITE); waits for the stream. */
 int se_batch_get_status(se_batch *batch, int *status);
+/* Stage timing of se_batch_evaluate: enable = 1 launches every kernel
+ * directly (no graph) with a CUDA event after each of the 8 stages (bin,
+ * scatter, spread, forward transform, scaling pass, inverse transform,
+ * gather, energy finish) and waits for them; se_batch_get_timing writes the
+ * summed milliseconds of each stage (nstages >= 8) and the number of timed
+ * evaluations, and clears them if reset. */
+int se_batch_set_timing(se_batch *batch, int enable);
+int se_batch_get_timing(se_batch *batch, double *ms, int nstages, int64_t *count, int reset);
 /* Autotuner: times `reps` evaluations with each tile edge in candidates[0..
  * ncand) (CUDA events, after warm-up) and keeps the fastest; reports it in
  * *best_tile and its time per evaluation in *best_ms. */

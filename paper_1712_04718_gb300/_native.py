@@ -68,6 +68,8 @@ SIGNATURES = {
     "se_batch_evaluate": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "se_batch_grid_energy": (_i, [_vp, _vp]),
     "se_batch_get_status": (_i, [_vp, ctypes.POINTER(_i)]),
+    "se_batch_set_timing": (_i, [_vp, _i]),
+    "se_batch_get_timing": (_i, [_vp, _dp, _i, ctypes.POINTER(_i64), _i]),
     "se_batch_autotune": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i, _i, ctypes.POINTER(_i),
                                ctypes.POINTER(ctypes.c_float)]),
     "se_real_create": (_i, [ctypes.POINTER(_vp), _i64, _d, _d, _d]),

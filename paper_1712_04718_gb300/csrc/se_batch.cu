@@ -400,6 +400,13 @@ struct se_batch {
     cudaStream_t cap = nullptr;
     cudaGraphExec_t gexec = nullptr;
     const void* gkey[5] = {};
+    // stage timing (se_batch_set_timing): an event after each of the 8 stages
+    static constexpr int kStages = 8;
+    bool timing = false;
+    bool ev_created = false;
+    cudaEvent_t ev[kStages + 1] = {};
+    double stage_ms[kStages] = {};
+    int64_t stage_count = 0;
 };
 
 namespace {
@@ -657,14 +664,21 @@ bool batch_gather_tiled(const se_batch* b) {
 int batch_launch(se_batch* b, const float* xyz, const float* q, float* F, float* phi, double* E,
                  cudaStream_t s) {
     cudaError_t e;
+    // stage timing: events between the launches (which then do not overlap)
+    auto mark = [&](int k) {
+        if (b->timing) cudaEventRecord(b->ev[k], s);
+    };
+    mark(0);
     const int nbin = (int)std::max(1LL, std::min((std::max(b->Ntot, b->Gtot) + 255) / 256, 4096LL));
     e = se::launch_ex(se::k_bbin, nbin, se::kThreads, 0, s, false, xyz, q, b->Ntot, b->S,
                       (const SysParams*)b->d_sys, b->tile_count, b->slot, b->tile_of, b->g64, b->Gtot);
     if (e != cudaSuccess) return SE_ERR_CUDA;
+    mark(1);
     e = se::launch_ex(se::k_bscatter, b->S, 1024, 0, s, true, xyz, q, (const SysParams*)b->d_sys,
                       b->tile_count, (const int*)b->slot, (const int*)b->tile_of, b->tile_start,
                       b->sorted, b->perm, b->d_bacc, b->S, b->Ntot);
     if (e != cudaSuccess) return SE_ERR_CUDA;
+    mark(2);
     switch (b->P) {
 #define SE_CASE(PP) case PP: e = launch_bspread<PP>(b, s); break;
         SE_FOR_EACH_P(SE_CASE)
@@ -672,6 +686,7 @@ int batch_launch(se_batch* b, const float* xyz, const float* q, float* F, float*
         default: return SE_ERR_UNSUPPORTED;
     }
     if (e != cudaSuccess) return SE_ERR_CUDA;
+    mark(3);
     const size_t slab = se::slab_smem_bytes(b->maxM);
     if (cudaFuncSetAttribute(se::k_bslab_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab) != cudaSuccess ||
         cudaFuncSetAttribute(se::k_bslab_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab) != cudaSuccess)
@@ -680,14 +695,17 @@ int batch_launch(se_batch* b, const float* xyz, const float* q, float* F, float*
                       b->cgrid, (const float2*)b->tw, (const SysParams*)b->d_sys,
                       (const BAcc*)b->d_bacc, (const int*)b->slab_sys);
     if (e != cudaSuccess) return SE_ERR_CUDA;
+    mark(4);
     e = se::launch_ex(se::k_bxpass, b->Xtot, se::kThreads, 0, s, true, b->cgrid, (const float2*)b->tw,
                       (const float*)b->green, (const SysParams*)b->d_sys, (const int*)b->x_sys,
                       b->x_part);
     if (e != cudaSuccess) return SE_ERR_CUDA;
+    mark(5);
     e = se::launch_ex(se::k_bslab_inv, b->Stot, se::kSlabThreads, slab, s, true, (const float2*)b->cgrid,
                       b->rgrid, (const float2*)b->tw, (const SysParams*)b->d_sys,
                       (const int*)b->slab_sys);
     if (e != cudaSuccess) return SE_ERR_CUDA;
+    mark(6);
     const bool tiled = batch_gather_tiled(b);
     switch (b->P) {
 #define SE_CASE(PP) \
@@ -697,13 +715,29 @@ int batch_launch(se_batch* b, const float* xyz, const float* q, float* F, float*
         default: return SE_ERR_UNSUPPORTED;
     }
     if (e != cudaSuccess) return SE_ERR_CUDA;
+    mark(7);
     e = se::launch_ex(se::k_bfinish, b->S, se::kThreads, 0, s, true, (const float*)b->e_part,
                       (const float*)b->e_tile, (int)tiled, (const float*)b->x_part,
                       (const SysParams*)b->d_sys, E, b->Eg);
-    return e == cudaSuccess ? SE_OK : SE_ERR_CUDA;
+    if (e != cudaSuccess) return SE_ERR_CUDA;
+    mark(8);
+    return SE_OK;
 }
 
 int batch_eval(se_batch* b, const void* xyz, const void* q, void* F, void* phi, double* E) {
+    if (b->timing) {   // direct launches with events between them; waits for the stages
+        const int rc = batch_launch(b, (const float*)xyz, (const float*)q, (float*)F, (float*)phi,
+                                    E, b->stream);
+        if (rc != SE_OK) return rc;
+        if (cudaEventSynchronize(b->ev[se_batch::kStages]) != cudaSuccess) return SE_ERR_CUDA;
+        for (int k = 0; k < se_batch::kStages; ++k) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, b->ev[k], b->ev[k + 1]) != cudaSuccess) return SE_ERR_CUDA;
+            b->stage_ms[k] += ms;
+        }
+        ++b->stage_count;
+        return SE_OK;
+    }
     if (b->use_graph) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         if (cudaStreamIsCapturing(b->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
@@ -776,7 +810,31 @@ int se_batch_destroy(se_batch* b) {
     if (!b) return SE_OK;
     free_all(b);
     if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->ev_created)
+        for (cudaEvent_t& e : b->ev) cudaEventDestroy(e);
     delete b;
+    return SE_OK;
+}
+
+int se_batch_set_timing(se_batch* b, int enable) {
+    if (!b) return SE_ERR_ARG;
+    if (enable && !b->ev_created) {
+        for (cudaEvent_t& e : b->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return SE_ERR_CUDA;
+        b->ev_created = true;
+    }
+    b->timing = enable != 0;
+    return SE_OK;
+}
+
+int se_batch_get_timing(se_batch* b, double* ms, int nstages, int64_t* count, int reset) {
+    if (!b || !ms || nstages < se_batch::kStages) return SE_ERR_ARG;
+    for (int k = 0; k < se_batch::kStages; ++k) ms[k] = b->stage_ms[k];
+    if (count) *count = b->stage_count;
+    if (reset) {
+        for (double& v : b->stage_ms) v = 0.0;
+        b->stage_count = 0;
+    }
     return SE_OK;
 }
 

@@ -434,6 +434,19 @@ class Batch:
         nat.check(self._lib.se_batch_grid_energy(self._h, _ptr(Eg)), "se_batch_grid_energy")
         return Eg
 
+    STAGES = ("bin", "scatter", "spread", "fft_fwd", "scale", "fft_inv", "gather", "finish")
+
+    def set_timing(self, enable=True):
+        nat.check(self._lib.se_batch_set_timing(self._h, int(bool(enable))), "se_batch_set_timing")
+
+    def get_timing(self, reset=True):
+        """(summed ms per stage as a dict, number of evaluations timed)."""
+        ms = (ctypes.c_double * 8)()
+        n = ctypes.c_int64()
+        nat.check(self._lib.se_batch_get_timing(self._h, ms, 8, ctypes.byref(n), int(reset)),
+                  "se_batch_get_timing")
+        return dict(zip(self.STAGES, list(ms))), n.value
+
     def status(self):
         st = ctypes.c_int()
         nat.check(self._lib.se_batch_get_status(self._h, ctypes.byref(st)), "se_batch_get_status")

@@ -96,6 +96,26 @@ def test_autotune_keeps_results():
     b.close()
 
 
+def test_batch_stage_timing_keeps_results():
+    """With stage timing on, the kernels run by direct launches with events
+    between the stages: the results are the graph replay's, and every one of
+    the 8 stages reports a positive time for each timed evaluation."""
+    xi, P = 4.0, 8
+    specs = small_ensemble(P, seed=5)
+    r = run_batch(specs, xi, P)
+    b = r["batch"]
+    b.set_timing(True)
+    for _ in range(3):
+        E, F, phi = b.evaluate(r["xd"], r["qd"])
+    torch.cuda.synchronize()
+    stages, n = b.get_timing()
+    b.set_timing(False)
+    assert n == 3 and len(stages) == 8 and all(v > 0 for v in stages.values())
+    assert rel(F.double().cpu().numpy(), r["F"]) < 1e-6
+    assert b.get_timing()[1] == 0   # cleared by the previous read
+    b.close()
+
+
 def test_batch_status_checks():
     xi, P = 4.0, 6
     specs = small_ensemble(P, seed=4)
