@@ -457,7 +457,11 @@ def run_ensemble(args, torch, se, ws, rank):
     b = se.Batch(Ns, [d["L"] for d in mine], [d["M"] for d in mine], w["xi"], w["P"])
     xd = torch.tensor(np.concatenate([d["x"] for d in mine]), device="cuda")
     qd = torch.tensor(np.concatenate([d["q"] for d in mine]), device="cuda")
-    tile, _, _ = tuning.tune_batch(b, xd, qd)
+    if args.tile:
+        b.set_tile(args.tile)
+        tile = args.tile
+    else:
+        tile, _, _ = tuning.tune_batch(b, xd, qd)
     Ntot = int(sum(Ns))
     F = torch.empty((Ntot, 3), dtype=torch.float32, device="cuda")
     phi = torch.empty((Ntot,), dtype=torch.float32, device="cuda")
