@@ -101,7 +101,9 @@ int se_plan_set_stream(se_plan *plan, void *stream);
  * one kernel adds every weight into a float grid with global reductions
  * (the last bits of the grid then depend on the order of the additions).
  * tile = edge of a spreading tile in grid cells (0 = automatic, else
- * 2..32).  For benchmarking and tests. */
+ * 2..32; for P <= 16 edges above 16 are reduced to 16, the largest the
+ * staged tile regions' fixed row stride holds).  For benchmarking and
+ * tests. */
 int se_plan_set_tuning(se_plan *plan, int spread_variant, int tile);
 
 /* Derived parameters: out[0..9] = h, w, eta, alpha, c_g, m, tile edge,
@@ -225,7 +227,8 @@ int se_batch_destroy(se_batch *batch);
 int se_batch_set_stream(se_batch *batch, void *stream);
 /* Multiply phi, E and F by kc (default 1). */
 int se_batch_set_prefactor(se_batch *batch, double kc);
-/* Edge of the spreading tiles in grid cells (2..32, default 8). */
+/* Edge of the spreading tiles in grid cells (2..32, default 8; for P <= 16
+ * edges above 16 are reduced to 16). */
 int se_batch_set_tile(se_batch *batch, int tile);
 /* enable = 0: launch every kernel directly instead of replaying a graph. */
 int se_batch_set_graph(se_batch *batch, int enable);

@@ -305,7 +305,8 @@ k_bgather_tile(const f4* __restrict__ sorted, const int* __restrict__ perm,
         tile_prep<P>(sorted[pb + group], kp, k, t0x, t0y, t0z, Ry, Rz, tp);
         orig = perm[pb + group];
     }
-    load_region(R + sp.g0, M, t0x - P / 2 + 1, t0y - P / 2 + 1, t0z - P / 2 + 1, Rx, Ry, Rz, reg);
+    load_region(R + sp.g0, M, t0x - P / 2 + 1, t0y - P / 2 + 1, t0z - P / 2 + 1, Rx, Ry, Rz,
+                region_stride<P>(Rz), reg);
     __syncthreads();
     df2 e_df = df_from(0.0f);
     for (int p0 = 0; p0 < n; p0 += ngroups) {
@@ -617,7 +618,8 @@ int prepare_batch(se_batch* b) {
 template <int P>
 cudaError_t launch_bspread(se_batch* b, cudaStream_t s) {
     const size_t R = (size_t)b->tile + P - 1;
-    const size_t plane = R * R * sizeof(unsigned);   // one 32-bit accumulator per point
+    // one 32-bit accumulator per point, rows padded to the region stride
+    const size_t plane = R * (size_t)se::region_stride<P>((int)R) * sizeof(unsigned);
     const int slab = (int)std::min(R, se::kSmemBudget / plane);
     if (slab < 1) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(se::k_bspread<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -642,7 +644,7 @@ cudaError_t launch_bgather(se_batch* b, float* phi, float* F, cudaStream_t s) {
 template <int P>
 cudaError_t launch_bgather_tile(se_batch* b, float* phi, float* F, cudaStream_t s) {
     const size_t R = (size_t)b->tile + P - 1;
-    const size_t bytes = R * R * R * sizeof(float);
+    const size_t bytes = R * R * (size_t)se::region_stride<P>((int)R) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(se::k_bgather_tile<P>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
@@ -656,8 +658,9 @@ cudaError_t launch_bgather_tile(se_batch* b, float* phi, float* F, cudaStream_t 
 // times the region) whose region fits the shared-memory budget.
 bool batch_gather_tiled(const se_batch* b) {
     const double R = (double)b->tile + b->P - 1;
+    const double RS = b->P <= 16 ? b->P + 15 : R;   // region_stride
     const double per_tile = (double)b->Ntot / std::max(1, b->Ttot);
-    return R * R * R * sizeof(float) <= (double)se::kTileGatherSmem &&
+    return R * R * RS * sizeof(float) <= (double)se::kTileGatherSmem &&
            per_tile * b->P * b->P * b->P >= 8.0 * R * R * R;
 }
 
@@ -853,6 +856,7 @@ int se_batch_set_prefactor(se_batch* b, double kc) {
 
 int se_batch_set_tile(se_batch* b, int tile) {
     if (!b || tile < 2 || tile > 32) return SE_ERR_ARG;
+    if (b->P <= 16 && tile > 16) tile = 16;   // the staged regions' row stride allows 16
     b->tile = tile;
     if (b->d_sys) return build_tables(b);
     return SE_OK;
@@ -910,7 +914,7 @@ int se_batch_autotune(se_batch* b, const void* xyz, const void* q, void* F, void
     float bms = 1e30f;
     for (int c = 0; c < ncand; ++c) {
         const int t = candidates[c];
-        if (t < 2 || t > 32) continue;
+        if (t < 2 || t > 32 || (b->P <= 16 && t > 16)) continue;
         b->tile = t;
         rc = build_tables(b);
         if (rc != SE_OK) continue;

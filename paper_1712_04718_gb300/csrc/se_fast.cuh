@@ -233,6 +233,20 @@ __device__ __forceinline__ void fx_split(float v, unsigned* vh, unsigned* vl) {
     }
 }
 
+// Row stride, in values, of a tile's region staged in shared memory (z
+// fastest, rows of the region's extent in z): for supports up to 16 a
+// compile-time P + 15, the extent of the largest tile edge used with them
+// (16), so that in the unrolled support loops every row offset is an
+// immediate of the load or atomic and only the plane step is an add; 0 (the
+// region's own extent) for larger supports.  Tile edges are at most 16 when
+// P <= 16 (the plan and the ensemble keep them there).
+template <int P>
+__host__ __device__ constexpr int region_pad() { return P <= 16 ? P + 15 : 0; }
+template <int P>
+__host__ __device__ constexpr int region_stride(int Rz) {
+    return region_pad<P>() > 0 ? region_pad<P>() : Rz;
+}
+
 // Spread of one tile (Eq. 3.5) into the fixed-point grid g64 (scale fxs =
 // 2^k): the n particles parts[0..n) of the tile.  The tile's region is
 // accumulated in shared memory as one 32-bit integer per point at the scale
@@ -259,7 +273,8 @@ __device__ __forceinline__ void spread_tile(const f4* __restrict__ parts, int n,
     const int t0x = tx * TT, t0y = ty * TT, t0z = tz * TT;
     const int Ry = min(TT, M - t0y) + P - 1, Rz = min(TT, M - t0z) + P - 1;
     const int Rx = min(TT, M - t0x) + P - 1;
-    const int plane = Ry * Rz;
+    const int RS = region_stride<P>(Rz);   // row stride of the staged region
+    const int plane = Ry * RS;
     const int shift = 10 + (n > 1 ? 32 - __clz(n - 1) : 0);   // 10 + ceil(log2 n)
     const float fxt = ldexpf(fxs, -shift);
 
@@ -302,7 +317,7 @@ __device__ __forceinline__ void spread_tile(const f4* __restrict__ parts, int n,
                 }
                 const float Bx = expf(2.0f * kp.beta * ux);
                 float px = expf(-kp.beta * ux * (ux + float(P - 1)) + 2.0f * kp.beta * ux * float(alo));
-                unsigned* row = acc + ((lx + alo - s0) * Ry + ly) * Rz + lz + k;
+                unsigned* row = acc + ((lx + alo - s0) * Ry + ly) * RS + lz + k;
                 // small supports: the z factors folded into the y factors
                 // (one multiply per weight); a running row pointer keeps the
                 // address of each atomic to one add
@@ -331,7 +346,7 @@ __device__ __forceinline__ void spread_tile(const f4* __restrict__ parts, int n,
                             for (int j = 0; j < D; ++j)
                                 atomicAdd(rb + j * G, (unsigned)__float2int_rn(wab * gz[j]));
                         }
-                        rb += Rz;
+                        rb += RS;
                     }
                     row += plane;
                 }
@@ -341,10 +356,11 @@ __device__ __forceinline__ void spread_tile(const f4* __restrict__ parts, int n,
         SE_STAMP(2, 3);
         const int ox = t0x - P / 2 + 1 + s0, oy = t0y - P / 2 + 1, oz = t0z - P / 2 + 1;
         const FDiv fRz = fdiv_of(Rz), fRy = fdiv_of(Ry);
-        for (int e = threadIdx.x; e < nel; e += blockDim.x) {
-            const int w = (int)acc[e];
+        const int nlog = ns * Ry * Rz;   // the region's points, without the row padding
+        for (int e = threadIdx.x; e < nlog; e += blockDim.x) {
+            const int r = fdiv(e, fRz), rz = e - r * Rz;
+            const int w = (int)acc[r * RS + rz];
             if (w != 0) {
-                const int r = fdiv(e, fRz), rz = e - r * Rz;
                 const int rx = fdiv(r, fRy), ry = r - rx * Ry;
                 const int gx_ = wrap_index(ox + rx, M), gy_ = wrap_index(oy + ry, M),
                           gz_ = wrap_index(oz + rz, M);
@@ -437,7 +453,8 @@ k_fspread(const f4* __restrict__ bucket, int cap, int* __restrict__ tile_count,
     if (ovf < 0) {
         const int nT = kp.nT, TT = kp.tile;
         const int ty = (tile / nT) % nT, tz = tile % nT, tx = tile / (nT * nT);
-        const int plane = (min(TT, kp.M - ty * TT) + P - 1) * (min(TT, kp.M - tz * TT) + P - 1);
+        const int plane = (min(TT, kp.M - ty * TT) + P - 1) *
+                          region_stride<P>(min(TT, kp.M - tz * TT) + P - 1);
         const int nel = min(slab, min(TT, kp.M - tx * TT) + P - 1) * plane;
         for (int e = threadIdx.x; e < nel; e += blockDim.x) sacc[e] = 0u;
     }
@@ -568,7 +585,7 @@ __device__ __forceinline__ void tile_prep(const f4& v, const KParams<float>& kp,
     g.Bx = expf(2.0f * kp.beta * g.ux);
     g.px0 = expf(-kp.beta * g.ux * (g.ux + float(P - 1)));
     g.q = v.w;
-    g.base = ((cx - t0x) * Ry + (cy - t0y)) * Rz + (cz - t0z) + k;
+    g.base = ((cx - t0x) * Ry + (cy - t0y)) * region_stride<P>(Rz) + (cz - t0z) + k;
 }
 
 template <int P>
@@ -580,7 +597,8 @@ __device__ __forceinline__ void tile_accum(const TilePrep<P>& g, const float* re
 #pragma unroll
     for (int j = 0; j < D; ++j) acc0[j] = accx[j] = accy[j] = 0.0f;
     float px = g.px0;
-    const int plane = Ry * Rz;
+    const int RS = region_stride<P>(Rz);
+    const int plane = Ry * RS;
 #pragma unroll(P <= 8 ? P : 1)
     for (int a = 0; a < P; ++a) {
         const float gxa = px * sE3[a];
@@ -598,7 +616,7 @@ __device__ __forceinline__ void tile_accum(const TilePrep<P>& g, const float* re
                 tb0[j] += g.gy[b] * hv;
                 tby[j] += g.dgy[b] * hv;
             }
-            rb += Rz;
+            rb += RS;
         }
 #pragma unroll
         for (int j = 0; j < D; ++j) {
@@ -617,9 +635,10 @@ __device__ __forceinline__ void tile_accum(const TilePrep<P>& g, const float* re
 }
 
 // Copy the grid over a tile region (origin o = tile origin - P/2 + 1, extent
-// Rx x Ry x Rz, wrapped periodically) into shared memory; the whole block.
+// Rx x Ry x Rz, wrapped periodically) into shared memory, rows RS values
+// apart (RS >= Rz); the whole block.
 __device__ __forceinline__ void load_region(const float* __restrict__ grid, int M, int ox, int oy,
-                                            int oz, int Rx, int Ry, int Rz, float* reg) {
+                                            int oz, int Rx, int Ry, int Rz, int RS, float* reg) {
     const int nel = Rx * Ry * Rz;
     const FDiv fRz = fdiv_of(Rz), fRy = fdiv_of(Ry);
     for (int e0 = threadIdx.x; e0 < nel; e0 += blockDim.x * kLoadBatch) {
@@ -637,7 +656,10 @@ __device__ __forceinline__ void load_region(const float* __restrict__ grid, int 
 #pragma unroll
         for (int u = 0; u < kLoadBatch; ++u) {
             const int e = e0 + u * (int)blockDim.x;
-            if (e < nel) reg[e] = v[u];
+            if (e < nel) {
+                const int r = fdiv(e, fRz);
+                reg[r * RS + (e - r * Rz)] = v[u];
+            }
         }
     }
 }
@@ -719,7 +741,8 @@ k_fgather(const f4* __restrict__ bucket, const int* __restrict__ bucket_idx, int
         }
         pdl_wait();
         SE_STAMP(6, 1);
-        load_region(grid, M, t0x - P / 2 + 1, t0y - P / 2 + 1, t0z - P / 2 + 1, Rx, Ry, Rz, reg);
+        load_region(grid, M, t0x - P / 2 + 1, t0y - P / 2 + 1, t0z - P / 2 + 1, Rx, Ry, Rz,
+                    region_stride<P>(Rz), reg);
         __syncthreads();
         SE_STAMP(6, 2);
         for (int p0 = 0; p0 < n; p0 += ngroups) {

@@ -41,7 +41,8 @@ inline int sm_count() {
 template <int P>
 cudaError_t fast_spread_P(const KParams<float>& kp, const FastBufs& b, int nbin, cudaStream_t s) {
     const size_t R = (size_t)kp.tile + P - 1;
-    const size_t plane = R * R * sizeof(unsigned);   // one 32-bit accumulator per point
+    // one 32-bit accumulator per point, rows padded to the region stride
+    const size_t plane = R * (size_t)region_stride<P>((int)R) * sizeof(unsigned);
     const int slab = (int)std::min(R, kSmemBudget / plane);
     if (slab < 1) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_fspread<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -170,7 +171,7 @@ cudaError_t fast_gather_P(const KParams<float>& kp, const FastBufs& b, float* ph
                           double* partials, unsigned* ticket, double e_scale, double* E_out,
                           const double* adj, cudaStream_t s) {
     const size_t R = (size_t)kp.tile + P - 1;
-    const size_t bytes = R * R * R * sizeof(float);
+    const size_t bytes = R * R * (size_t)region_stride<P>((int)R) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_fgather<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)bytes);
     if (e != cudaSuccess) return e;
@@ -187,8 +188,9 @@ cudaError_t fast_gather_P(const KParams<float>& kp, const FastBufs& b, float* ph
 // partials' space.
 bool fast_gather_tiled(const KParams<float>& kp) {
     const double R = (double)kp.tile + kp.P - 1;
+    const double RS = kp.P <= 16 ? kp.P + 15 : R;   // region_stride
     const double per_tile = (double)kp.N / kp.ntiles;
-    return R * R * R * sizeof(float) <= (double)kTileGatherSmem &&
+    return R * R * RS * sizeof(float) <= (double)kTileGatherSmem &&
            kp.ntiles + kOverflowBlocks <= 4 * kMaxPartials &&
            per_tile * kp.P * kp.P * kp.P >= 8.0 * R * R * R;
 }

@@ -176,6 +176,7 @@ void derive(se_plan* p) {
     p->cg = pow(2.0 * p->xi * p->xi / (kPi * p->eta), 1.5);
     // spreading variant and tile edge
     int tile = p->tune_tile > 0 ? p->tune_tile : 8;
+    if (p->P <= 16 && tile > 16) tile = 16;   // the staged regions' row stride allows 16
     if (tile > p->M) tile = p->M;
     p->tile = tile;
     p->nT = (p->M + tile - 1) / tile;
