@@ -279,7 +279,10 @@ k_bgather_tile(const f4* __restrict__ sorted, const int* __restrict__ perm,
                const int* __restrict__ tile_start, const float* __restrict__ R,
                const SysParams* __restrict__ sys, const int* __restrict__ tile_sys,
                float* __restrict__ phi, float* __restrict__ F, float* __restrict__ e_tile) {
-    constexpr int D = pick_d(P), G = P / D, GPW = 32 / G;
+    // two z points per lane for small supports (half the lanes of k_gather per
+    // particle): the per-particle set-up and the lane reduction are shared by
+    // fewer lanes, each with twice the grid points
+    constexpr int D = P <= 8 ? 2 * pick_d(P) : pick_d(P), G = P / D, GPW = 32 / G;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* reg = reinterpret_cast<float*>(smem_raw);
     __shared__ df2 sbuf[32];
@@ -299,10 +302,10 @@ k_bgather_tile(const f4* __restrict__ sorted, const int* __restrict__ perm,
     pdl_wait();
     pdl_launch_next();
     const int pb = tile_start[blockIdx.x], n = tile_start[blockIdx.x + 1] - pb;
-    TilePrep<P> tp;
+    TilePrep<P, D> tp;
     int orig = -1;
     if (gi < GPW && group < n) {
-        tile_prep<P>(sorted[pb + group], kp, k, t0x, t0y, t0z, Ry, Rz, tp);
+        tile_prep<P, D>(sorted[pb + group], kp, k, t0x, t0y, t0z, Ry, Rz, tp);
         orig = perm[pb + group];
     }
     load_region(R + sp.g0, M, t0x - P / 2 + 1, t0y - P / 2 + 1, t0z - P / 2 + 1, Rx, Ry, Rz,
@@ -315,12 +318,12 @@ k_bgather_tile(const f4* __restrict__ sorted, const int* __restrict__ perm,
         float vphi = 0.0f, vfx = 0.0f, vfy = 0.0f, vfz = 0.0f;
         if (valid) {
             if (p0 != 0) {
-                tile_prep<P>(sorted[pb + p], kp, k, t0x, t0y, t0z, Ry, Rz, tp);
+                tile_prep<P, D>(sorted[pb + p], kp, k, t0x, t0y, t0z, Ry, Rz, tp);
                 orig = perm[pb + p];
             }
-            tile_accum<P>(tp, reg, Ry, Rz, sE3, vphi, vfx, vfy, vfz);
+            tile_accum<P, D>(tp, reg, Ry, Rz, sE3, vphi, vfx, vfy, vfz);
         }
-        gather_emit<P>(k, valid, orig, tp.q, vphi, vfx, vfy, vfz, kp, phi, F, 1.0f, 1.0f, e_df);
+        gather_emit<P, G>(k, valid, orig, tp.q, vphi, vfx, vfy, vfz, kp, phi, F, 1.0f, 1.0f, e_df);
     }
     const df2 r = block_sum_df(e_df, sbuf);
     if (threadIdx.x == 0) {

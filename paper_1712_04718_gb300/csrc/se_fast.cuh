@@ -554,18 +554,18 @@ k_fspread(const f4* __restrict__ bucket, int cap, int* __restrict__ tile_count,
 // grid.  The particles' factors are computed before the dependent-launch
 // wait.  Outputs go to the particles' input positions; the energy
 // 1/2 sum q phi is reduced as in k_gather.
-template <int P>
+template <int P, int DD = pick_d(P)>
 struct TilePrep {
-    static constexpr int D = pick_d(P);
+    static constexpr int D = DD;
     float gy[P], dgy[P], gz[D], dgz[D];
     float ux, px0, Bx, q;
     int base;   // region offset of support point (0, 0, this lane's first z)
 };
 
-template <int P>
+template <int P, int DD = pick_d(P)>
 __device__ __forceinline__ void tile_prep(const f4& v, const KParams<float>& kp, int k, int t0x,
-                                          int t0y, int t0z, int Ry, int Rz, TilePrep<P>& g) {
-    constexpr int D = pick_d(P), G = P / D;
+                                          int t0y, int t0z, int Ry, int Rz, TilePrep<P, DD>& g) {
+    constexpr int D = DD, G = P / D;
     float t;
     const int cx = cell_of(v.x, kp.invh, kp.M, &t);
     g.ux = centre_offset(t, cx);
@@ -588,11 +588,11 @@ __device__ __forceinline__ void tile_prep(const f4& v, const KParams<float>& kp,
     g.base = ((cx - t0x) * Ry + (cy - t0y)) * region_stride<P>(Rz) + (cz - t0z) + k;
 }
 
-template <int P>
-__device__ __forceinline__ void tile_accum(const TilePrep<P>& g, const float* reg, int Ry, int Rz,
-                                           const float* sE3, float& vphi, float& vfx, float& vfy,
-                                           float& vfz) {
-    constexpr int D = pick_d(P), G = P / D;
+template <int P, int DD = pick_d(P)>
+__device__ __forceinline__ void tile_accum(const TilePrep<P, DD>& g, const float* reg, int Ry,
+                                           int Rz, const float* sE3, float& vphi, float& vfx,
+                                           float& vfy, float& vfz) {
+    constexpr int D = DD, G = P / D;
     float acc0[D], accx[D], accy[D];
 #pragma unroll
     for (int j = 0; j < D; ++j) acc0[j] = accx[j] = accy[j] = 0.0f;
@@ -666,13 +666,12 @@ __device__ __forceinline__ void load_region(const float* __restrict__ grid, int 
 
 // Sum over the G lanes of a particle, then lane 0 of the group writes phi and
 // F at the particle's input position and adds q phi to the energy.
-template <int P>
+template <int P, int G = P / pick_d(P)>
 __device__ __forceinline__ void gather_emit(int k, bool valid, int orig, float qq, float vphi,
                                             float vfx, float vfy, float vfz,
                                             const KParams<float>& kp, float* __restrict__ phi,
                                             float* __restrict__ F, float phi_mul, float F_mul,
                                             df2& e_df) {
-    constexpr int G = P / pick_d(P);
 #pragma unroll
     for (int o = 1; o < G; o <<= 1) {
         const float a0 = __shfl_down_sync(0xffffffffu, vphi, o);
