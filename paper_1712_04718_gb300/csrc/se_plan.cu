@@ -452,14 +452,16 @@ int fast_scale(se_plan* p, double* E_grid) {
 
 int fast_gather(se_plan* p, void* phi, void* F, double* E, const double* adj = nullptr) {
     const KParams<float> kp = make_kparams<float>(p);
-    if (p->variant == 3 && (F || adj) && se::fast_gather_tiled(kp)) {
+    // dense tiles: the tile gather, with or without forces (it stages the
+    // grid once per tile, which outweighs the force sums it then skips)
+    if (p->variant == 3 && se::fast_gather_tiled(kp)) {
         SE_CUDA(se::fast_gather(kp, fast_bufs(p), (float*)phi, (float*)F,
                                 p->partials + 4 * se::kMaxPartials, p->tickets + 2, 0.5, E, adj,
                                 p->stream));
         timing_mark(p, 6);
         return SE_OK;
     }
-    if (!F && !adj) {   // potential (and energy) only: the plain window
+    if (!F && !adj) {   // potential (and energy) only, L2 reads: the plain window
         SE_CUDA(se::launch_gather_plain<float>(1, (const se::f4*)p->sorted, nullptr,
                                                (const float*)p->grid_gather,
                                                (size_t)p->M * p->M * p->M, (float*)phi, nullptr, kp,
