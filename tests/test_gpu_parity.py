@@ -462,6 +462,12 @@ def test_tile_gather_dense_tiles():
     assert abs(g["E"] - r["E"]) < 5 * TOL["fp32"] * abs(r["E"])
     g4 = run_gpu(x, q, L, xi, M, P, "fp32", spread_variant=3, tile=4)   # sparse tiles
     assert rel(g["F"], g4["F"]) < 1e-6 and rel(g["phi"], g4["phi"]) < 1e-6
+    # potential only (F = NULL) keeps the tile gather: the same phi and energy
+    plan = se.Plan(N, L, xi, M, P, precision="fp32", spread_variant=3, tile=6)
+    E_p, phi_p = plan.potential(torch.tensor(x, device="cuda"), torch.tensor(q, device="cuda"))
+    plan.close()
+    assert rel(phi_p.double().cpu().numpy(), g["phi"]) < 1e-6
+    assert abs(E_p - g["E"]) < 1e-6 * abs(g["E"])
 
 
 def test_tile_gather_with_overflow():
