@@ -290,6 +290,19 @@ class RealSpace:
 
     def evaluate(self, xyz, q, F=None, phi=None, E=None, accumulate=False):
         """Device tensors (plan dtype); E: CUDA float64 tensor of one element."""
+        if self.N > 0:
+            for name, t, shape in (("xyz", xyz, (self.N, 3)), ("q", q, (self.N,)),
+                                   ("F", F, (self.N, 3)), ("phi", phi, (self.N,))):
+                if t is None:
+                    if name in ("xyz", "q"):
+                        raise ValueError("%s is required" % name)
+                    continue
+                if t.dtype != self.dtype or not t.is_cuda or not t.is_contiguous() or \
+                        tuple(t.shape) != shape:
+                    raise TypeError("%s must be a contiguous CUDA %s tensor of shape %s"
+                                    % (name, self.dtype, shape))
+        if E is not None and (E.dtype != torch.float64 or not E.is_cuda or E.numel() < 1):
+            raise TypeError("E must be a CUDA float64 tensor")
         s = torch.cuda.current_stream().cuda_stream
         nat.check(self._lib.se_real_set_stream(self._h, ctypes.c_void_p(s)), "se_real_set_stream")
         nat.check(self._lib.se_real_evaluate(self._h, _ptr(xyz), _ptr(q), _ptr(F), _ptr(phi),
