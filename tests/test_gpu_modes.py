@@ -177,3 +177,19 @@ def test_adjoint_is_analytic_in_ik_mode():
     plan.close()
     assert rel(gx.cpu().numpy(), -2.0 * ref["F"]) < 1e-12
     assert rel(gq.cpu().numpy(), 2.0 * ref["phi"]) < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_modes_empty_system(prec):
+    """N = 0 in every mode: zero energy, no output touched, no error."""
+    L, xi, M, P = 2.0, 3.0, 16, 6
+    for mode in ("analytic", "ik"):
+        plan = se.Plan(0, L, xi, M, P, precision=prec, force_mode=mode)
+        x = torch.empty((0, 3), dtype=plan.dtype, device="cuda")
+        q = torch.empty((0,), dtype=plan.dtype, device="cuda")
+        E, F, phi = plan.energy_force(x, q)
+        assert E == 0.0 and F.shape == (0, 3)
+        assert plan.energy(x, q) == 0.0
+        E_p, _ = plan.potential(x, q)
+        assert E_p == 0.0
+        plan.close()

@@ -157,3 +157,15 @@ def test_real_space_accumulate_and_empty():
     torch.cuda.synchronize()
     assert E0.item() == 0.0
     empty.close()
+
+
+def test_real_space_cell_cap_sparse_box():
+    """A sparse 20 nm box with rc = 0.4 nm: K L / rc = 100 cells per dimension
+    are capped at 40 (edge 0.5 nm >= rc / 2); against the oracle's image sum."""
+    L, xi, rc = 20.0, 8.0, 0.4
+    x, q = systems.uniform_charges(3000, L, seed=4)
+    g = run_real(x, q, L, xi, rc, "fp64")
+    assert g["cells"] == 40
+    r = oracle.ewald_real(x, q, L, xi, rc)
+    assert rel(g["phi"], r["phi_real"] + r["phi_self"]) < TOL["fp64"]
+    assert rel(g["F"], r["F_real"]) < TOL["fp64"]
