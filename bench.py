@@ -434,6 +434,8 @@ def run_ours(args):
         out["autograd"] = autograd_timing(se, torch, x, q, w, prec, max(20, min(K, 500)), flush)
         out["modes"] = other_modes(se, torch, x, q, w, prec, min(K, 500), flush, (variant, tile))
         out["real_space"] = real_space(se, torch, x, q, w, prec, min(K, 500), flush, plan)
+        if prec != "fp64":
+            out["xi_balance"] = xi_balance(se, torch, x, q, w, prec)
         out["cpu_baseline"] = cpu_baseline(x, q, w, args.cpu_seconds)
     plan.close()
     if ws > 1:
@@ -837,6 +839,34 @@ def real_space(se, torch, x, q, w, prec, K, flush, plan):
                            "kind": "oracle", "sample": "%d target atoms of the box (all images "
                            "within rc), scaled to all %d" % (ns, N)}
     return out
+
+
+def xi_balance(se, torch, x, q, w, prec):
+    """The splitting-parameter balance of the paper's Sec. 6.2 on this machine:
+    the whole Ewald evaluation (k-space plan, then the real-space sum) timed
+    against the real-space cut-off, hence xi, at a fixed rms force tolerance
+    of 1e-3 of the box's rms total force, each cut-off with the parameters
+    se_select_params gives (tuning.tune_ewald).  The fastest is the balance."""
+    from paper_1712_04718_gb300 import tuning
+    N = len(q)
+    rprec = "fp64" if prec == "fp64" else "fp32"
+    dt = torch.float64 if rprec == "fp64" else torch.float32
+    xd = torch.tensor(x, dtype=dt, device="cuda")
+    qd = torch.tensor(q, dtype=dt, device="cuda")
+    plan = se.Plan(N, w["L"], w["xi"], w["M"], w["P"], precision=prec)
+    rs = se.RealSpace(N, w["L"], w["xi"], min(1.0, w["L"] / 3.0), precision=rprec)
+    F = torch.empty((N, 3), dtype=dt, device="cuda")
+    phi = torch.empty((N,), dtype=dt, device="cuda")
+    Ed = torch.zeros(1, dtype=torch.float64, device="cuda")
+    plan.evaluate(xd, qd, F, phi, Ed)
+    rs.evaluate(xd, qd, F, phi, Ed, accumulate=True)
+    f_rms = float(torch.sqrt((F.double() ** 2).sum(1).mean()))
+    plan.close()
+    rs.close()
+    tol = 1e-3 * f_rms
+    best, table = tuning.tune_ewald(xd, qd, w["L"], tol, precision=rprec)
+    return {"tol_rel_to_rms_force": 1e-3, "tol_abs": tol, "best": best, "table": table,
+            "note": "se_select_params sizes each error source to tol (the paper's estimates)"}
 
 
 def no_graph(se, torch, plan, xd, qd, F, phi, Ed, flush, K):

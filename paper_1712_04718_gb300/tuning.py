@@ -107,3 +107,48 @@ def tune_batch(batch, xyz, q, candidates=(6, 8, 10, 12, 16), reps=10, use_cache=
     tile, ms = batch.autotune(xyz, q, candidates=candidates, reps=reps)
     _store(key, {"tile": tile, "ms": ms})
     return tile, ms, False
+
+
+def tune_ewald(xyz, q, L, tol, quantity="force", rc_candidates=None, precision="fp32", reps=20):
+    """Measured balance of the real-space and Fourier-space parts of the whole
+    Ewald sum.  The fastest splitting parameter xi for a tolerance balances
+    the costs of the two parts and depends on the implementation and the
+    hardware (arXiv:1712.04718, Sec. 6.2).  For each real-space cut-off rc
+    (default: six values from 0.5 to min(1.6, L/3)), the parameters
+    se_select_params gives for the absolute rms tolerance tol (xi from rc, M,
+    P), and the whole evaluation -- the k-space plan, then the real-space sum
+    accumulated into the same outputs -- are timed on the caller's system
+    (CUDA device tensors xyz [N, 3], q [N] of the precision's dtype).
+    Returns (best, table): dicts with rc, xi, M, P and the milliseconds of the
+    k-space part, the real-space part and the whole evaluation."""
+    import numpy as np
+    from . import se
+    N = int(q.shape[0])
+    Q = float((q.double() ** 2).sum())
+    if rc_candidates is None:
+        rc_candidates = [round(float(r), 3) for r in np.linspace(0.5, min(1.6, L / 3.0), 6)]
+    table = []
+    for rc in rc_candidates:
+        s = se.select_params(quantity, tol, rc, L, Q)
+        if not s["supported"] or rc > L / 3.0:
+            continue
+        plan = se.Plan(N, L, s["xi"], s["M"], s["P"], precision=precision)
+        rs = se.RealSpace(N, L, s["xi"], rc, precision=precision)
+        F = torch.empty((N, 3), dtype=plan.dtype, device=xyz.device)
+        phi = torch.empty((N,), dtype=plan.dtype, device=xyz.device)
+        E = torch.zeros(1, dtype=torch.float64, device=xyz.device)
+        ms_k = _time(lambda: plan.evaluate(xyz, q, F, phi, E), reps)
+        ms_r = _time(lambda: rs.evaluate(xyz, q, F, phi, E, accumulate=True), reps)
+
+        def whole():
+            plan.evaluate(xyz, q, F, phi, E)
+            rs.evaluate(xyz, q, F, phi, E, accumulate=True)
+        ms_t = _time(whole, reps)
+        table.append({"rc": rc, "xi": s["xi"], "M": s["M"], "P": s["P"], "ms_kspace": ms_k,
+                      "ms_real": ms_r, "ms_total": ms_t})
+        plan.close()
+        rs.close()
+    if not table:
+        raise ValueError("no cut-off in %s gives supported parameters for tol %g"
+                         % (list(rc_candidates), tol))
+    return min(table, key=lambda r: r["ms_total"]), table

@@ -169,3 +169,32 @@ def test_real_space_cell_cap_sparse_box():
     r = oracle.ewald_real(x, q, L, xi, rc)
     assert rel(g["phi"], r["phi_real"] + r["phi_self"]) < TOL["fp64"]
     assert rel(g["F"], r["F_real"]) < TOL["fp64"]
+
+
+def test_tune_ewald_picks_the_fastest_within_tolerance():
+    """Measured xi balancing: over three cut-offs, the fastest whole-Ewald
+    evaluation at the parameters se_select_params gives; its force error
+    against the converged Ewald total stays within 2 tol."""
+    from paper_1712_04718_gb300 import tuning
+    L, tol = 3.0, 1e-3
+    x, q = systems.water_box(L, seed=6)
+    xd = torch.as_tensor(x, dtype=torch.float64).cuda().contiguous()
+    qd = torch.as_tensor(q, dtype=torch.float64).cuda().contiguous()
+    best, table = tuning.tune_ewald(xd, qd, L, tol, rc_candidates=(0.6, 0.8, 1.0),
+                                    precision="fp64", reps=5)
+    assert len(table) == 3
+    assert best["ms_total"] == min(r["ms_total"] for r in table)
+    assert all(r["ms_kspace"] > 0 and r["ms_real"] > 0 for r in table)
+    plan = se.Plan(len(q), L, best["xi"], best["M"], best["P"], precision="fp64")
+    rs = se.RealSpace(len(q), L, best["xi"], best["rc"], precision="fp64")
+    F = torch.empty((len(q), 3), dtype=torch.float64, device="cuda")
+    phi = torch.empty(len(q), dtype=torch.float64, device="cuda")
+    E = torch.zeros(1, dtype=torch.float64, device="cuda")
+    plan.evaluate(xd, qd, F, phi, E)
+    rs.evaluate(xd, qd, F, phi, E, accumulate=True)
+    torch.cuda.synchronize()
+    plan.close()
+    rs.close()
+    _, _, F_t = oracle.ewald_total(x, q, L, best["xi"])
+    err = math.sqrt(((F.cpu().numpy() - F_t) ** 2).sum(1).mean())
+    assert err <= 2 * tol, (best, err)
