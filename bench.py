@@ -155,7 +155,7 @@ def dft_split(M):
     return best
 
 
-def stage_work(w, prec, N, variant):
+def stage_work(w, prec, N, variant, tile=0):
     """Algorithmic work of each own kernel per launch: (kind, amount, kernel).
 
     spread (variants 3, 4): N P^3 weights; in the sorted pipeline each is one
@@ -180,7 +180,8 @@ def stage_work(w, prec, N, variant):
     work = {
         "spread": (("smem_atomic", float(N) * P ** 3, "k_fspread") if variant == 3 else
                    ("flop", 2.0 * N * P ** 3, "k_fdirect" if variant == 4 else "k_spread")),
-        "gather": ("flop", 4.0 * N * P ** 3, "k_gather"),
+        "gather": ("flop", 4.0 * N * P ** 3, "k_fgather" if variant == 3 and
+                   tile_gather_selected(N, M, P, tile) else "k_gather"),
         "bin": ("byte", N * (4 * ts + 8), "k_fbin" if variant == 3 else "k_bin"),
         "scatter": ("byte", N * (4 * ts + 4 * ts + 8 + 4), "k_scatter"),
     }
@@ -191,6 +192,21 @@ def stage_work(w, prec, N, variant):
     else:
         work["scale"] = ("byte", nc * (4 * ts + 8) + M ** 3 * ts, "k_scale")
     return work
+
+
+def tile_gather_selected(N, M, P, tile):
+    """Whether the single-precision pipeline gathers with its tile kernel
+    (k_fgather) rather than k_gather: the library's own rule (dense tiles,
+    mean particles per tile x P^3 >= 8 x region, the region with its padded
+    rows within 64 KB), restated here only to name the kernel."""
+    if not tile:
+        return False
+    R = tile + P - 1
+    RS = P + 15 if P <= 16 else R
+    nT = (M + tile - 1) // tile
+    ntiles = nT ** 3
+    return (R * R * RS * 4 <= 64 * 1024 and ntiles + 8 <= 4096 and
+            (N / ntiles) * P ** 3 >= 8.0 * R ** 3)
 
 
 def kernel_sources_sha():
@@ -371,7 +387,7 @@ def run_ours(args):
 
     # roofline of the dominant own kernel (average launch duration from events)
     fast = variant in (3, 4)
-    work = stage_work(w, prec, N, variant)
+    work = stage_work(w, prec, N, variant, int(tile or 0))
     per_launch_ms = {k: v / max(1, nstage) for k, v in stages.items()}
     own = [k for k in ("bin", "scatter", "spread", "scale", "gather") if k in work]
     if fast:
