@@ -444,9 +444,9 @@ int rs_run(se_real* r, const void* xyz, const void* q, void* F, void* phi, doubl
 
 }  // namespace
 
-// Cells per dimension and stencil reach for (N, L, rc); reach_user 1-3
-// forces K (SE_ERR_UNSUPPORTED if its 2K+1 cells do not fit), 0 chooses.
-static int rs_layout(int64_t N, double L, double rc, int reach_user, int* K_out, int* nc_out) {
+// Cells per dimension and stencil reach for (L, rc); reach_user 1-3 forces
+// K (SE_ERR_UNSUPPORTED if its 2K+1 cells do not fit), 0 chooses.
+static int rs_layout(double L, double rc, int reach_user, int* K_out, int* nc_out) {
     if (floor(L / rc) < 3.0) return SE_ERR_UNSUPPORTED;   // r_c > L/3
     // stencil reach K: cells of edge >= rc/K, nc >= 2K+1 distinct images
     // (rc <= L/3 gives floor(2 L / rc) >= 6); K = 2 by default (a 5^3 stencil:
@@ -458,7 +458,6 @@ static int rs_layout(int64_t N, double L, double rc, int reach_user, int* K_out,
     auto cells_for = [&](int K) {
         return (int)std::min<double>(floor(K * L / rc), kMaxCellsPerDim);
     };
-    (void)N;
     int K = 2;
     if (reach_user >= 1) K = reach_user;
     else if (cells_for(3) >= 7 && cells_for(2) * cells_for(2) * cells_for(2) < 512)
@@ -476,7 +475,7 @@ extern "C" int se_real_create(se_real** out, int64_t N, double L, double xi, dou
         !isfinite(xi) || !(rc > 0.0) || !isfinite(rc))
         return SE_ERR_ARG;
     int K = 0, nc = 0;
-    const int st = rs_layout(N, L, rc, 0, &K, &nc);
+    const int st = rs_layout(L, rc, 0, &K, &nc);
     if (st != SE_OK) return st;
     se_real* r = new (std::nothrow) se_real;
     if (!r) return SE_ERR_NOMEM;
@@ -494,7 +493,7 @@ extern "C" int se_real_create(se_real** out, int64_t N, double L, double xi, dou
 extern "C" int se_real_set_reach(se_real* r, int K) {
     if (!r || K < 0 || K > 3) return SE_ERR_ARG;
     int Kn = 0, nc = 0;
-    const int st = rs_layout(r->N, r->L, r->rc, K, &Kn, &nc);
+    const int st = rs_layout(r->L, r->rc, K, &Kn, &nc);
     if (st != SE_OK) return st;
     if (nc * nc * nc != r->ncells) rs_release(r);   // buffers sized by the cell count
     r->K = Kn;
