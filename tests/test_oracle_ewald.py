@@ -163,3 +163,14 @@ def test_kolafa_perram_fourier_estimate():
         est = xi / (L * math.pi) * math.sqrt(8.0 / kinf) * Q * math.exp(-(math.pi * kinf / (xi * L)) ** 2)
         est_rms = est / math.sqrt(N)
         assert 0.5 < err / est_rms < 2.0, (kinf, err, est_rms)
+
+
+def test_real_space_at_targets_equals_full_sum():
+    """ewald_real_at at a sample of particles equals the full real-space sum
+    there (same images, cut-off and terms), bit for bit."""
+    x, q = systems.uniform_charges(300, 2.0, seed=1)
+    r = oracle.ewald_real(x, q, 2.0, 4.0, 0.6)
+    idx = [0, 7, 150, 299]
+    ph, F = oracle.ewald_real_at(x, q, 2.0, 4.0, 0.6, idx)
+    assert np.array_equal(ph, r["phi_real"][idx])
+    assert np.array_equal(F, r["F_real"][idx])
