@@ -551,3 +551,48 @@ def test_largest_support_single_precision():
     r = oracle_for(x, q, L, xi, M, P, "fp32")
     assert rel(g["F"], r["F"]) < 5 * TOL["fp32"]
     assert rel(g["phi"], r["phi"]) < 5 * TOL["fp32"]
+
+
+def _random_configs(n, seed):
+    """Seeded random (N, L, xi, M, P, tile) with a valid eta (Eq. 4.2)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < n:
+        M = int(rng.integers(8, 49))
+        P = int(rng.choice([2, 4, 6, 8, 10, 12, 14, 16]))
+        if P > M:
+            continue
+        L = float(rng.uniform(1.0, 4.0))
+        xi = float(rng.uniform(2.0, 6.0))
+        eta = P * L * L * xi * xi / (0.95 ** 2 * math.pi * M * M)
+        if not (0.05 < eta < 0.9):
+            continue
+        tile = int(rng.choice([0, 2, 3, 4, 5, 6, 8, 12, 16]))
+        N = int(rng.choice([0, 1, 2, 37, 500, 3000]))
+        out.append((N, L, xi, M, P, tile))
+    return out
+
+
+@pytest.mark.parametrize("cfg", _random_configs(12, seed=2024))
+def test_random_configurations_single_precision(cfg):
+    """The single-precision pipeline (variant 3) on random sizes, supports,
+    tile edges and particle counts against the oracle."""
+    N, L, xi, M, P, tile = cfg
+    x, q = systems.uniform_charges(max(N, 1), L, seed=N + M, dtype=np.float32)
+    x, q = x[:N], q[:N]
+    if N % 2:
+        q = q.copy()
+        q[-1] = -q[:-1].sum() if N > 1 else q[-1]
+    g = run_gpu(x, q, L, xi, M, P, "fp32", spread_variant=3, tile=tile)
+    if N == 0:
+        assert g["E"] == 0.0
+        return
+    r = oracle_for(x, q, L, xi, M, P, "fp32")
+    # the force's rounding scale is that of its terms, q xi |phi| per particle:
+    # for one or two charges the net force is a small remainder (zero by
+    # symmetry up to the approximation error), so the bound takes both scales
+    dF = np.linalg.norm(g["F"] - r["F"])
+    scale = np.linalg.norm(r["F"]) + xi * np.linalg.norm(np.asarray(q, np.float64) * r["phi"])
+    assert dF < 5 * TOL["fp32"] * scale, cfg
+    assert rel(g["phi"], r["phi"]) < 5 * TOL["fp32"], cfg
+    assert abs(g["E"] - r["E"]) < 5 * TOL["fp32"] * abs(r["E"]) + 1e-12, cfg
