@@ -19,3 +19,16 @@ def test_cost_model_units():
 def test_profiled_traffic_needs_matching_sources():
     assert bench.profiled_traffic("k_gather", "no-such-workload") is None
     assert bench.profiled_traffic("no_such_kernel", "water-L6-M52-P6-fp32comp") is None
+
+
+def test_tile_gather_rule_names_the_kernel():
+    """The bench names the gather kernel by the library's rule: dense tiles
+    (the 100k-atom box, tile edge 8) use the tile gather, the 21.6k-atom box
+    at tile edge 6 and an automatic tile do not; a region past 64 KB never."""
+    assert bench.tile_gather_selected(100200, 84, 8, 8)
+    assert not bench.tile_gather_selected(21642, 52, 6, 6)
+    assert not bench.tile_gather_selected(21642, 52, 6, 0)
+    assert not bench.tile_gather_selected(10 ** 7, 128, 24, 16)
+    w = {"P": 8, "M": 84}
+    assert bench.stage_work(w, "fp32comp", 100200, 3, 8)["gather"][2] == "k_fgather"
+    assert bench.stage_work(w, "fp32comp", 100200, 4, 8)["gather"][2] == "k_gather"
