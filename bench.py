@@ -46,7 +46,9 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="bounded CPU work of the cpu_baseline leg")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip accuracy, e2e, at-target and cpu_baseline legs")
+                    help="skip the legs after the headline: accuracy, e2e, at-target, no-graph, "
+                         "unsorted variant, autograd, evaluation modes, real space, xi balance "
+                         "and cpu_baseline")
     ap.add_argument("--tile", type=int, default=0,
                     help="spreading tile edge (0 = autotune, JSON-cached)")
     ap.add_argument("--variant", type=int, default=-1,
