@@ -289,7 +289,9 @@ int se_spread_noalloc(const double *xyz, const double *q, int64_t N, double L, d
  * force and energy.  Cells of edge >= rc/K hold the particles (K L/rc per
  * dimension, at most 40; K = 2, or 3 when K = 2 gives fewer than 512 cells;
  * se_real_get_cells reports the count, se_real_set_reach overrides K);
- * rc > L/3 returns SE_ERR_UNSUPPORTED at creation.
+ * se_real_create returns SE_ERR_ARG for N < 0 or N >= 2^31, or a
+ * non-positive or non-finite L, xi or rc, and SE_ERR_UNSUPPORTED for
+ * rc > L/3.
  * se_real_evaluate: xyz [N][3], q [N], F [N][3], phi [N] DEVICE arrays of the
  * precision's type (SE_FP64 double, SE_FP32 float), E a DEVICE double; F,
  * phi and E may be NULL.  accumulate = 0 overwrites the outputs, 1 adds to
@@ -325,9 +327,10 @@ int se_real_evaluate(se_real *real, const void *xyz, const void *q, void *F, voi
  *          and to P, and rounded up to even.
  * c: the shape constant of Eq. 4.2 (0 selects 0.95).  Writes *xi, *M, *P
  * and, if k_inf is not NULL, the unrounded k_inf.  Returns SE_ERR_ARG for a
- * non-positive or non-finite tol, rc, L or Q, or an unknown quantity;
- * SE_ERR_UNSUPPORTED when the tolerance is met with no Fourier part or the
- * selected P exceeds 32 (the outputs are still written in that case). */
+ * non-positive or non-finite tol, rc, L or Q, a negative c, a NULL xi, M or
+ * P, or an unknown quantity; SE_ERR_UNSUPPORTED, with nothing written, when
+ * the tolerance is met without a Fourier part or needs k_inf above 1e6, and
+ * SE_ERR_UNSUPPORTED with the outputs written when the selected P exceeds 32. */
 #define SE_QUANTITY_POTENTIAL 0
 #define SE_QUANTITY_ENERGY 1
 #define SE_QUANTITY_FORCE 2
