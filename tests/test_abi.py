@@ -105,6 +105,11 @@ def test_real_space_arguments(lib):
         assert lib.se_real_set_prefactor(h, -1.0) == nat.SE_ERR_ARG
         assert lib.se_real_destroy(h) == nat.SE_OK
     assert lib.se_real_destroy(None) == nat.SE_OK
+    # missing inputs are rejected before any device call
+    assert lib.se_real_create(ctypes.byref(h), 10, 3.0, 3.0, 1.0) == nat.SE_OK
+    assert lib.se_real_evaluate(h, None, None, None, None, None, 0) == nat.SE_ERR_ARG
+    assert lib.se_real_evaluate(None, None, None, None, None, None, 0) == nat.SE_ERR_ARG
+    assert lib.se_real_destroy(h) == nat.SE_OK
 
 
 @pytest.mark.parametrize("L,xi,M,P", [(3.0, 3.5, 32, 16), (6.0, 3.12, 52, 6), (10.0, 3.12, 84, 8)])
