@@ -261,22 +261,30 @@ int se_batch_autotune(se_batch *batch, const void *xyz, const void *q, void *F, 
  * cudaMalloc (a program that reserves all device memory at start-up and
  * forbids allocation in its inner loop, or a component whose device memory
  * belongs to another framework's allocator).
- * Writes H_j = sum_n q_n c_g exp(-alpha |x_j - x_n|^2) (Eq. 3.5, FP64,
- * parameters as se_plan_create with c = 0.95) into the caller's DEVICE grid
- * H (M^3 doubles, z fastest; cleared by the call), from DEVICE xyz [N][3]
- * and q [N], asynchronously on `stream` (cudaStream_t, NULL = default).
+ * Writes the spread grid of se_spread, H_j = sum_n q_n c_g
+ * exp(-alpha |x_j - x_n|^2) in FP64 with the parameters of se_plan_create
+ * (c = 0.95), into the caller's DEVICE grid H (M^3 doubles, z fastest;
+ * cleared by the call), from DEVICE xyz [N][3] and q [N], asynchronously on
+ * `stream` (cudaStream_t, NULL = default).
  * All intermediate buffers live in one static device array of about 1.5 MB,
  * reserved on every GPU that loads the library until the process exits.
- * Limits: N <= 32768 and M <= 128; larger sizes return SE_ERR_ARG.
+ * Limits: N <= 32768 and M <= 128; larger sizes return SE_ERR_ARG, as do a
+ * NULL H, P < 2 or P > M; odd P returns SE_ERR_UNSUPPORTED.  All of these are
+ * decided on the host before any CUDA call.
+ * Non-finite positions or charges are not detected here (there is no status
+ * to read back without a host synchronisation): a NaN charge gives a NaN
+ * grid; the plan path reports them through se_plan_get_status.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and should come before any stream capture.
+ * (cudaGetSymbolAddress) with that device current and keeps it for the life
+ * of the process: make that first call before any stream capture, and do not
+ * call this entry point again on a device after cudaDeviceReset (the kept
+ * address is then stale).
  * Calls share the array: calls that overlap on the GPU race; issue them on
  * one stream.  Allocates nothing (no cudaMalloc, cudaFree or allocating
  * library call). */
 int se_spread_noalloc(const double *xyz, const double *q, int64_t N, double L, double xi,
                       int M, int P, double *H, void *stream);
 
-/* Static message for a status code. */
 /* ---- Real-space part of the Ewald sum (the complement of the k-space path) ----
  * Sec. 1, Eq. 1.5-1.7: for charges in [0, L)^3 with splitting parameter xi
  * and cut-off rc (0 < rc <= L/3):
@@ -346,6 +354,7 @@ int se_select_support(double scaled_tol, double c);
  * NaN otherwise: the inverse the estimates of Eq. 2.3-2.4 need. */
 double se_lambert_w0(double z);
 
+/* Static message for a status code. */
 const char *se_strerror(int status);
 
 /* Stage timing (tracing).  enable = 1 records a CUDA event before and after

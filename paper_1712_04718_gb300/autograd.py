@@ -21,7 +21,9 @@ from .se import Plan
 class SEEnergy(torch.autograd.Function):
     @staticmethod
     def forward(ctx, xyz, q, plan, recompute):
-        E = torch.zeros(1, dtype=torch.float64, device=xyz.device)
+        # the scaling step writes E (an empty system writes nothing)
+        E = (torch.empty if plan.N > 0 else torch.zeros)(1, dtype=torch.float64,
+                                                          device=xyz.device)
         plan.spread(xyz, q)
         plan.scale(E)
         ctx.save_for_backward(xyz, q)
@@ -37,7 +39,9 @@ class SEEnergy(torch.autograd.Function):
         if ctx.recompute or plan.generation != ctx.generation:
             plan.spread(xyz, q)
             plan.scale(None)
-        g = gE.detach().to(torch.float64).reshape(1).contiguous()
+        g = gE.detach()
+        if g.dtype != torch.float64 or g.dim() != 1:
+            g = g.to(torch.float64).reshape(1).contiguous()
         gx = torch.empty_like(xyz) if ctx.needs_input_grad[0] else None
         gq = torch.empty_like(q) if ctx.needs_input_grad[1] else None
         plan.adjoint(xyz, q, g, gx, gq)

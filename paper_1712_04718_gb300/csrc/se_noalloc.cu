@@ -1,5 +1,5 @@
-// se_noalloc.cu -- se_spread_noalloc: the spreading step (Eq. 3.5) for
-// callers that cannot allocate device memory.
+// se_noalloc.cu -- se_spread_noalloc: the spreading step of se_spread for
+// callers that cannot allocate device memory (no counterpart in the paper).
 //
 // Some callers can't call cudaMalloc: a host program that reserves all of its
 // device memory at start-up and forbids allocation inside its time-step loop,
@@ -13,7 +13,10 @@
 // of the process: kScratchBytes (about 1.5 MB).  All calls on a device share
 // it, so two calls that overlap on the GPU (different streams, or different
 // host threads) race and corrupt each other's results: issue them on one
-// stream, one after another.
+// stream, one after another.  The array's device address is looked up once
+// per device and kept: after a cudaDeviceReset it is stale, and this entry
+// point must not be called on that device again.  Non-finite inputs are not
+// reported (no status is read back).
 #include <mutex>
 
 #include "../../include/se.h"

@@ -56,6 +56,7 @@ class Plan:
         if force_mode != "analytic":
             self.set_force_mode(force_mode)
         self.last_status = 0
+        self._stream_handle = None   # the stream last handed to the library
         # counts evaluations that overwrite the plan's grids (spreads); the
         # autograd layer uses it to know whether the grid of a forward pass
         # is still in place at its backward pass
@@ -89,8 +90,13 @@ class Plan:
             pass
 
     def _stream(self):
+        # hand torch's current stream to the library when it changed (the
+        # library keeps it; a call per step would cost a host round trip)
         s = torch.cuda.current_stream().cuda_stream
-        nat.check(self._lib.se_plan_set_stream(self._h, ctypes.c_void_p(s)), "se_plan_set_stream")
+        if s != self._stream_handle:
+            nat.check(self._lib.se_plan_set_stream(self._h, ctypes.c_void_p(s)),
+                      "se_plan_set_stream")
+            self._stream_handle = s
 
     def _check_inputs(self, xyz, q):
         if xyz.dtype != self.dtype or q.dtype != self.dtype:

@@ -126,23 +126,37 @@ def ensemble(S=64, Lmin=3.0, Lmax=7.0, spacing=0.12, seed_L=999, seed0=1000,
     return out
 
 
-# Named workloads: box, Ewald parameter, grid, support, precision.
+# Named workloads: box, Ewald parameter, grid, support, precision, and the
+# relative rms force error each is held to.  target_source says where that
+# error comes from: "stated" when the workload's own description gives it,
+# "chosen" when it does not (the 100 200-atom box states none; 5e-4 is the
+# value picked here, between the 1e-3 of the 21 642-atom box and the 1e-4
+# of the ensemble).  The "-P8" water box and the "-P10" ensemble are the
+# stated workloads at the smallest even support that meets the stated error
+# (P = 6 gives 3e-3 on the 21 642-atom box, P = 8 about 3e-4 on the
+# ensemble); the stated settings stay in the table and are measured too.
 WORKLOADS = {
     "uniform-1000-L3-M32-P16-fp64": dict(
         kind="uniform", N=1000, L=3.0, xi=3.5, M=32, P=16, prec="fp64", seed=1,
-        target_rel_force_err=1e-8),
+        target_rel_force_err=1e-8, target_source="stated"),
     "water-L6-M52-P6-fp32comp": dict(
         kind="water", L=6.0, xi=3.12, M=52, P=6, prec="fp32comp", seed=2,
-        target_rel_force_err=1e-3),
+        target_rel_force_err=1e-3, target_source="stated"),
+    "water-L6-M52-P8-fp32comp": dict(
+        kind="water", L=6.0, xi=3.12, M=52, P=8, prec="fp32comp", seed=2,
+        target_rel_force_err=1e-3, target_source="stated"),
     "water-L6-M96-P24-fp64": dict(
         kind="water", L=6.0, xi=3.12, M=96, P=24, prec="fp64", seed=2,
-        target_rel_force_err=1e-10),
+        target_rel_force_err=1e-10, target_source="stated"),
     "water-L10-M84-P8-fp32comp": dict(
         kind="water", L=10.0, xi=3.12, M=84, P=8, prec="fp32comp", seed=4,
-        target_rel_force_err=5e-4),
+        target_rel_force_err=5e-4, target_source="chosen"),
     "ensemble-64-water-L3to7-P8-fp32comp": dict(
         kind="ensemble", S=64, xi=3.12, P=8, prec="fp32comp", spacing=0.12,
-        target_rel_force_err=1e-4),
+        target_rel_force_err=1e-4, target_source="stated"),
+    "ensemble-64-water-L3to7-P10-fp32comp": dict(
+        kind="ensemble", S=64, xi=3.12, P=10, prec="fp32comp", spacing=0.12,
+        target_rel_force_err=1e-4, target_source="stated"),
 }
 
 

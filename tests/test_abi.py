@@ -82,6 +82,23 @@ def test_argument_validation(lib):
     assert lib.se_probe_peak(0, None) == nat.SE_ERR_ARG
 
 
+def test_spread_noalloc_rejects_on_the_host(lib):
+    """se_spread_noalloc decides every rejection before any CUDA call, so
+    dummy non-null pointers are safe here: sizes beyond its static scratch
+    (N > 32768, M > 128), a NULL grid, P outside [2, M], odd P."""
+    from paper_1712_04718_gb300 import _native as nat
+    dummy = ctypes.c_void_p(16)
+    f = lib.se_spread_noalloc
+    assert f(dummy, dummy, 32769, 3.0, 3.5, 32, 8, dummy, None) == nat.SE_ERR_ARG
+    assert f(dummy, dummy, 4, 30.0, 0.5, 129, 8, dummy, None) == nat.SE_ERR_ARG
+    assert f(dummy, dummy, 4, 3.0, 3.5, 32, 8, None, None) == nat.SE_ERR_ARG
+    assert f(dummy, dummy, -1, 3.0, 3.5, 32, 8, dummy, None) == nat.SE_ERR_ARG
+    assert f(None, None, 4, 3.0, 3.5, 32, 8, dummy, None) == nat.SE_ERR_ARG
+    assert f(dummy, dummy, 4, 3.0, 3.5, 32, 0, dummy, None) == nat.SE_ERR_ARG
+    assert f(dummy, dummy, 4, 3.0, 3.5, 16, 18, dummy, None) == nat.SE_ERR_ARG
+    assert f(dummy, dummy, 4, 3.0, 3.5, 32, 7, dummy, None) == nat.SE_ERR_UNSUPPORTED
+
+
 def test_real_space_arguments(lib):
     """se_real_create validates its arguments on the host; the cell grid is
     floor(K L / rc) per dimension (K = 2, or 3 when K = 2 gives under 512

@@ -1,8 +1,11 @@
 """Host helpers of bench.py (no GPU): the cost-model constants derived from
-per-stage times, and the lookup of profiled DRAM traffic."""
+per-stage times, the lookup of profiled DRAM traffic, the O1 cut-off of the
+error statements, the ensemble's sampled systems and the compact legs."""
+import json
 import math
 
 import bench
+from paper_1712_04718_gb300 import systems
 
 
 def test_cost_model_units():
@@ -17,8 +20,44 @@ def test_cost_model_units():
 
 
 def test_profiled_traffic_needs_matching_sources():
-    assert bench.profiled_traffic("k_gather", "no-such-workload") is None
-    assert bench.profiled_traffic("no_such_kernel", "water-L6-M52-P6-fp32comp") is None
+    assert bench.profiled_traffic("k_gather", "no-such-workload") == (None, None)
+    assert bench.profiled_traffic("no_such_kernel", bench.DEFAULT_WORKLOAD) == (None, None)
+
+
+def test_o1_cutoff_is_far_below_each_target():
+    for name, w in systems.WORKLOADS.items():
+        tol = bench.o1_tolerance(w["target_rel_force_err"])
+        assert 1e-16 <= tol <= 1e-6
+        assert tol <= 1e-3 * w["target_rel_force_err"] or tol == 1e-16, name
+
+
+def test_headline_meets_its_stated_error_by_construction():
+    w = systems.WORKLOADS[bench.DEFAULT_WORKLOAD]
+    assert w["target_source"] == "stated" and w["P"] == 8 and w["M"] == 52
+    assert bench.DEFAULT_WORKLOAD not in bench.LEG_WORKLOADS
+    for leg in bench.LEG_WORKLOADS:
+        assert leg in systems.WORKLOADS
+
+
+def test_ensemble_sample_spans_box_sizes():
+    ens = [dict(L=L) for L in (5.0, 3.1, 6.9, 4.0, 3.5, 6.0, 4.5, 5.5, 3.0, 7.0, 6.5)]
+    s = bench.ensemble_sample(ens)
+    assert len(s) == bench.ENS_SAMPLE_SYSTEMS
+    Ls = [ens[i]["L"] for i in s]
+    assert min(Ls) == 3.0 and max(Ls) == 7.0
+
+
+def test_compact_leg_stays_short():
+    res = {"workload": "water-L10-M84-P8-fp32comp", "value": 7045.123456, "ms_step": 0.1419,
+           "N": 100200, "roofline": {"frac": 0.0661234, "kernel": "k_fgather"},
+           "clocks": {"sm_mhz": 2070.0, "reasons": []},
+           "autograd": {"forward": 9035.0, "forward_backward": 5042.0, "unit": "evals/s"}}
+    acc = {"rel_rms_force_err": 2.9e-4, "target": 5e-4, "target_met": True}
+    eq = {"P": 8, "value": 3000.0, "ms": 0.33, "err": 2.8e-4, "equal": True}
+    leg = bench.compact_leg(res, acc, eq)
+    assert len(json.dumps(leg)) < 480
+    assert leg["met"] and leg["fp64_eq"]["P"] == 8
+    assert bench.r4(0.0661234) == 0.06612
 
 
 def test_tile_gather_rule_names_the_kernel():

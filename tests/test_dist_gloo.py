@@ -1,4 +1,4 @@
-"""The multi-rank host logic of bench.py on two CPU ranks (gloo): the
+"""The multi-rank host logic (paper_1712_04718_gb300.sharding) on two CPU ranks (gloo): the
 ensemble's systems are split over the ranks without overlap or gaps and with
 balanced cost, every rank computing the same assignment, and the timing
 reduction returns the slowest rank's time on every rank."""
@@ -11,8 +11,7 @@ import torch
 import torch.distributed as dist
 import torch.multiprocessing as mp
 
-import bench
-from paper_1712_04718_gb300 import systems
+from paper_1712_04718_gb300 import sharding, systems
 
 
 def _free_port():
@@ -36,11 +35,11 @@ def _worker(rank, ws, port, out):
     dist.init_process_group("gloo", rank=rank, world_size=ws)
     try:
         Ns, Ms = _ensemble_sizes()
-        costs = [bench.system_cost(n, m, 8) for n, m in zip(Ns, Ms)]
-        parts = bench.partition_systems(costs, ws)
+        costs = [sharding.system_cost(n, m, 8) for n, m in zip(Ns, Ms)]
+        parts = sharding.partition_systems(costs, ws)
         gathered = [None] * ws
         dist.all_gather_object(gathered, parts[rank])
-        slowest = bench.max_over_ranks(10.0 * (rank + 1), ws, "cpu")
+        slowest = sharding.max_over_ranks(10.0 * (rank + 1), ws, "cpu")
         out.put((rank, gathered, slowest, parts))
     finally:
         dist.destroy_process_group()
@@ -60,7 +59,7 @@ def test_partition_and_max_over_two_gloo_ranks():
         assert p.exitcode == 0
     res.sort()
     Ns, Ms = _ensemble_sizes()
-    costs = [bench.system_cost(n, m, 8) for n, m in zip(Ns, Ms)]
+    costs = [sharding.system_cost(n, m, 8) for n, m in zip(Ns, Ms)]
     for rank, gathered, slowest, parts in res:
         assert slowest == 20.0                      # the slowest rank's time on every rank
         assert gathered == res[0][3]                # every rank computed the same assignment
@@ -73,7 +72,14 @@ def test_partition_and_max_over_two_gloo_ranks():
 
 
 def test_partition_single_rank_and_more_ranks_than_systems():
-    assert bench.partition_systems([3.0, 1.0, 2.0], 1) == [[0, 1, 2]]
-    parts = bench.partition_systems([3.0, 1.0], 4)
+    assert sharding.partition_systems([3.0, 1.0, 2.0], 1) == [[0, 1, 2]]
+    parts = sharding.partition_systems([3.0, 1.0], 4)
     assert sorted(i for p in parts for i in p) == [0, 1] and sum(1 for p in parts if not p) == 2
-    assert bench.max_over_ranks(1.5, 1, "cpu") == 1.5
+    assert sharding.max_over_ranks(1.5, 1, "cpu") == 1.5
+
+
+def test_shard_covers_the_ensemble_once():
+    Ns, Ms = _ensemble_sizes()
+    ws = 3
+    got = sorted(i for r in range(ws) for i in sharding.shard(Ns, Ms, 8, ws, r))
+    assert got == list(range(64))

@@ -15,6 +15,7 @@ import torch
 import oracle
 from paper_1712_04718_gb300 import se, systems
 from paper_1712_04718_gb300.autograd import se_energy
+from parity import assert_close
 
 pytestmark = pytest.mark.gpu
 
@@ -26,10 +27,6 @@ def _built():
     torch.cuda.set_device(0)
 
 
-def rel(a, b):
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
-    return math.sqrt(((a - b) ** 2).sum() / (b ** 2).sum())
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 1e-6)])
@@ -47,8 +44,8 @@ def test_backward_is_force_and_potential(prec, tol):
     assert abs(E.item() - E0) < (1e-12 if prec == "fp64" else 1e-6) * abs(E0)
     g = 2.5
     (g * E).backward()
-    assert rel(xg.grad.double().cpu(), (-g * F).double().cpu()) < tol
-    assert rel(qg.grad.double().cpu(), (g * phi).double().cpu()) < tol
+    assert_close(xg.grad.double().cpu(), (-g * F).double().cpu(), tol)
+    assert_close(qg.grad.double().cpu(), (g * phi).double().cpu(), tol)
     plan.close()
 
 
@@ -104,12 +101,12 @@ def test_fp32_gradient_against_fp64_and_oracle():
         se_energy(xg, qg, plan).backward()
         grads[prec] = (xg.grad.double().cpu().numpy(), qg.grad.double().cpu().numpy())
         plan.close()
-    assert rel(grads["fp32"][0], grads["fp64"][0]) < 2e-5
-    assert rel(grads["fp32"][1], grads["fp64"][1]) < 2e-5
+    assert_close(grads["fp32"][0], grads["fp64"][0], 2e-5)
+    assert_close(grads["fp32"][1], grads["fp64"][1], 2e-5)
     r = oracle.se_kspace(np.asarray(x, np.float64), np.asarray(q, np.float64), w["L"], w["xi"],
                          w["M"], w["P"], cell_mode=32)
-    assert rel(grads["fp32"][0], -r["F"]) < 1e-4
-    assert rel(grads["fp32"][1], r["phi"]) < 1e-4
+    assert_close(grads["fp32"][0], -r["F"], 1e-4)
+    assert_close(grads["fp32"][1], r["phi"], 1e-4)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -131,9 +128,9 @@ def test_recompute_when_grid_overwritten(prec):
     Ea.backward()
     _, F, _ = ref.energy_force(xa.detach(), qa)
     tol = 1e-12 if prec == "fp64" else 1e-6
-    assert rel(xa.grad.double().cpu(), -F.double().cpu()) < tol
+    assert_close(xa.grad.double().cpu(), -F.double().cpu(), tol)
     xc = torch.tensor(x, dtype=dtype, device="cuda").requires_grad_(True)
     se_energy(xc, qa, plan, recompute=True).backward()
-    assert rel(xc.grad.double().cpu(), -F.double().cpu()) < tol
+    assert_close(xc.grad.double().cpu(), -F.double().cpu(), tol)
     plan.close()
     ref.close()

@@ -15,8 +15,16 @@ import torch
 import oracle
 from paper_1712_04718_gb300 import _native as nat
 from paper_1712_04718_gb300 import se, systems
+from parity import assert_close, normwise
 
 pytestmark = pytest.mark.gpu
+
+# single precision against the oracle: 2e-5 on grids, 5 x 2e-5 on the
+# particles' outputs (a few hundred rounding steps deeper), as in the
+# single-system parity tests; a system of a batch and its own single-system
+# evaluation run the same arithmetic in the same order, hence 1e-6
+TOL_FP32 = 2e-5
+TOL_SAME = 1e-6
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -26,10 +34,6 @@ def _built():
     torch.cuda.set_device(0)
 
 
-def rel(a, b):
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
-    return math.sqrt(((a - b) ** 2).sum() / (b ** 2).sum())
 
 
 def small_ensemble(P, seed=0):
@@ -72,14 +76,15 @@ def test_batch_equals_single_systems_and_oracle(P, graph):
         E1, F1, phi1 = plan.energy_force(torch.tensor(d["x"], device="cuda"),
                                          torch.tensor(d["q"], device="cuda"))
         plan.close()
-        assert rel(r["F"][sl], F1.double().cpu().numpy()) < 1e-6, s
-        assert rel(r["phi"][sl], phi1.double().cpu().numpy()) < 1e-6, s
+        assert_close(r["F"][sl], F1.double().cpu().numpy(), TOL_SAME, q=d["q"], label=s)
+        assert_close(r["phi"][sl], phi1.double().cpu().numpy(), TOL_SAME, label=s)
         assert abs(r["E"][s] - E1) < 1e-6 * abs(E1), s
         assert abs(r["Eg"][s] - E1) < 2e-5 * abs(E1), s
         o = oracle.se_kspace(d["x"].astype(np.float64), d["q"].astype(np.float64), d["L"], xi,
                              d["M"], P, cell_mode=32)
-        assert rel(r["F"][sl], o["F"]) < 1e-4, s
-        assert abs(r["E"][s] - o["E"]) < 1e-4 * abs(o["E"]), s
+        assert_close(r["F"][sl], o["F"], 5 * TOL_FP32, q=d["q"], label=s)
+        assert_close(r["phi"][sl], o["phi"], 5 * TOL_FP32, label=s)
+        assert abs(r["E"][s] - o["E"]) < 5 * TOL_FP32 * abs(o["E"]), s
     r["batch"].close()
 
 
@@ -92,7 +97,7 @@ def test_autotune_keeps_results():
     assert tile in (4, 6, 8) and ms > 0
     E, F, phi = b.evaluate(r["xd"], r["qd"])
     torch.cuda.synchronize()
-    assert rel(F.double().cpu().numpy(), r["F"]) < 1e-6
+    assert_close(F.double().cpu().numpy(), r["F"], 1e-6)
     b.close()
 
 
@@ -111,7 +116,7 @@ def test_batch_stage_timing_keeps_results():
     stages, n = b.get_timing()
     b.set_timing(False)
     assert n == 3 and len(stages) == 8 and all(v > 0 for v in stages.values())
-    assert rel(F.double().cpu().numpy(), r["F"]) < 1e-6
+    assert_close(F.double().cpu().numpy(), r["F"], 1e-6)
     assert b.get_timing()[1] == 0   # cleared by the previous read
     b.close()
 
@@ -131,30 +136,59 @@ def test_batch_status_checks():
     r["batch"].close()
 
 
-def test_water_ensemble_64():
-    """The 64-box water ensemble (L ~ U[3, 7] nm, 0.12 nm grid spacing,
-    P = 8): a few systems against their single-system evaluation and the
-    direct Ewald sum on sampled atoms.  P = 8 gives about 3e-4 relative rms
-    force error (the stated 1e-4 needs P = 10)."""
+@pytest.fixture(scope="module")
+def water_ensemble():
     w = systems.WORKLOADS["ensemble-64-water-L3to7-P8-fp32comp"]
-    ens = systems.ensemble(S=w["S"], spacing=w["spacing"])
-    P, xi = w["P"], w["xi"]
+    return w, systems.ensemble(S=w["S"], spacing=w["spacing"])
+
+
+@pytest.mark.parametrize("P", [8, 10])
+def test_water_ensemble_64_every_system_against_oracle(water_ensemble, P):
+    """The 64-box water ensemble (L ~ U[3, 7] nm, 0.12 nm grid spacing, M
+    from 25 to 60): every system, element by element, against the oracle's
+    plain SE of that system (float32 cell decisions), and a few systems
+    against their own single-system evaluation."""
+    w, ens = water_ensemble
+    xi = w["xi"]
     r = run_batch(ens, xi, P)
     assert r["status"] == nat.SE_OK
     off = np.concatenate([[0], np.cumsum([len(d["q"]) for d in ens])])
-    rng = np.random.default_rng(5)
-    for s in (0, 17, 63):
+    for s, d in enumerate(ens):
+        sl = slice(off[s], off[s + 1])
+        o = oracle.se_kspace(d["x"].astype(np.float64), d["q"].astype(np.float64), d["L"], xi,
+                             d["M"], P, cell_mode=32)
+        assert_close(r["F"][sl], o["F"], 5 * TOL_FP32, q=d["q"], label=(s, d["M"]))
+        assert_close(r["phi"][sl], o["phi"], 5 * TOL_FP32, label=(s, d["M"]))
+        assert abs(r["E"][s] - o["E"]) < 5 * TOL_FP32 * abs(o["E"]), s
+    Ms = [d["M"] for d in ens]
+    for s in (int(np.argmin(Ms)), int(np.argmax(Ms))):
         d = ens[s]
         sl = slice(off[s], off[s + 1])
         plan = se.Plan(len(d["q"]), d["L"], xi, d["M"], P, precision="fp32")
         E1, F1, _ = plan.energy_force(torch.tensor(d["x"], device="cuda"),
                                       torch.tensor(d["q"], device="cuda"))
         plan.close()
-        assert rel(r["F"][sl], F1.double().cpu().numpy()) < 1e-6
+        assert_close(r["F"][sl], F1.double().cpu().numpy(), TOL_SAME, q=d["q"], label=s)
+    r["batch"].close()
+
+
+def test_water_ensemble_64_P10_meets_stated_error(water_ensemble):
+    """At P = 10 every one of the 64 systems meets the stated relative rms
+    force error of 1e-4 against the direct Ewald sum (O1 at 64 sampled atoms
+    of each system; P = 8 gives about 3e-4)."""
+    w, ens = water_ensemble
+    xi, P = w["xi"], 10
+    r = run_batch(ens, xi, P)
+    off = np.concatenate([[0], np.cumsum([len(d["q"]) for d in ens])])
+    rng = np.random.default_rng(6)
+    errs = []
+    for s, d in enumerate(ens):
+        sl = slice(off[s], off[s + 1])
         x64, q64 = d["x"].astype(np.float64), d["q"].astype(np.float64)
         idx = rng.choice(len(q64), 64, replace=False)
-        nmax = oracle.nmax_for(xi, d["L"], 1e-12)
+        nmax = oracle.nmax_for(xi, d["L"], 1e-8)
         S_ = oracle.ewald_structure(x64, q64, d["L"], nmax)
         _, Fo = oracle.ewald_eval(x64[idx], q64[idx], S_, d["L"], xi, nmax)
-        assert rel(r["F"][sl][idx], Fo) < 6e-4, s
+        errs.append(normwise(r["F"][sl][idx], Fo))
     r["batch"].close()
+    assert max(errs) <= w["target_rel_force_err"], (int(np.argmax(errs)), max(errs))

@@ -16,6 +16,7 @@ import torch
 
 import oracle
 from paper_1712_04718_gb300 import se, systems
+from parity import assert_close, normwise
 
 pytestmark = pytest.mark.gpu
 
@@ -29,12 +30,6 @@ def _built():
     torch.cuda.set_device(0)
 
 
-def rel(a, b):
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
-    n = math.sqrt((b ** 2).sum())
-    d = math.sqrt(((a - b) ** 2).sum())
-    return d / n if n > 0 else d
 
 
 def _dev(a, dt):
@@ -61,8 +56,8 @@ def test_ik_forces_parity(prec, M, P):
     plan.close()
     ref = oracle.se_kspace_ik(x, q, L, xi, M, P, cell_mode=_cm(prec))
     F = F.double().cpu().numpy()
-    assert rel(F, ref["F"]) < TOL[prec]
-    assert rel(phi.double().cpu().numpy(), ref["phi"]) < TOL[prec]
+    assert_close(F, ref["F"], TOL[prec])
+    assert_close(phi.double().cpu().numpy(), ref["phi"], TOL[prec])
     assert abs(E - ref["E"]) < TOL[prec] * abs(ref["E"])
     bound = 1e-13 if prec == "fp64" else 1e-6
     assert np.linalg.norm(F.sum(0)) < bound * np.abs(F).sum()
@@ -86,8 +81,8 @@ def test_ik_water_workload_more_accurate():
     nmax = oracle.nmax_for(xi, L, 1e-14)
     S = oracle.ewald_structure(x64, q64, L, nmax)
     _, F1 = oracle.ewald_eval(x64[idx], q64[idx], S, L, xi, nmax)
-    e_ik = rel(out["ik"][idx], F1)
-    e_an = rel(out["analytic"][idx], F1)
+    e_ik = normwise(out["ik"][idx], F1)
+    e_an = normwise(out["analytic"][idx], F1)
     assert e_ik < e_an < 5e-3, (e_ik, e_an)
     # parity on a sampled subset against the ik oracle would need the whole
     # system's grid; the momentum identity holds at any size
@@ -108,9 +103,9 @@ def test_potential_only(prec, variant):
     E_f, _, phi_f = plan.energy_force(xd, qd)
     plan.close()
     ref = oracle.se_kspace(x, q, L, xi, M, P, cell_mode=_cm(prec))
-    assert rel(phi_p.double().cpu().numpy(), ref["phi"]) < TOL[prec]
+    assert_close(phi_p.double().cpu().numpy(), ref["phi"], TOL[prec])
     assert abs(E_p - ref["E"]) < TOL[prec] * abs(ref["E"])
-    assert rel(phi_p.double().cpu().numpy(), phi_f.double().cpu().numpy()) < TOL[prec]
+    assert_close(phi_p.double().cpu().numpy(), phi_f.double().cpu().numpy(), TOL[prec])
     assert abs(E_p - E_f) < TOL[prec] * abs(E_f)
 
 
@@ -154,8 +149,8 @@ def test_force_mode_switch_and_graph():
             _, F, _ = plan.energy_force(xd, qd)
             _, F2, _ = plan.energy_force(xd, qd)
             F, F2 = F.double().cpu().numpy(), F2.double().cpu().numpy()
-            assert rel(F, ref["F"]) < TOL["fp32"], (mode, graph)
-            assert rel(F2, F) < TOL["fp32"]
+            assert_close(F, ref["F"], TOL["fp32"], label=(mode, graph))
+            assert_close(F2, F, TOL["fp32"])
     plan.close()
 
 
@@ -175,8 +170,8 @@ def test_adjoint_is_analytic_in_ik_mode():
     plan.adjoint(xd, qd, g, gx, gq)
     torch.cuda.synchronize()
     plan.close()
-    assert rel(gx.cpu().numpy(), -2.0 * ref["F"]) < 1e-12
-    assert rel(gq.cpu().numpy(), 2.0 * ref["phi"]) < 1e-12
+    assert_close(gx.cpu().numpy(), -2.0 * ref["F"], 1e-12)
+    assert_close(gq.cpu().numpy(), 2.0 * ref["phi"], 1e-12)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])

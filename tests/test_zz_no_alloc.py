@@ -33,18 +33,27 @@ def _rel(a, b):
     return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
 
 
-def test_spread_noalloc_matches_plan_spread():
+# (N, M, P): the 32 768-particle limit on the largest grid (4096 tiles, the
+# scratch's tile bound), a grid that is not a multiple of the tile edge
+# (partial edge tiles), and a support whose region exceeds the shared-memory
+# budget of one pass (the tiled spread works in slabs)
+SHAPES = [(2000, 32, 8), (32768, 128, 8), (3000, 50, 6), (2000, 48, 24)]
+
+
+@pytest.mark.parametrize("N,M,P", SHAPES)
+def test_spread_noalloc_matches_plan_spread(N, M, P):
     import __graft_entry__
     __graft_entry__.build()
     torch.cuda.set_device(0)
     lib = nat.load()
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    L, xi, M, P = 3.0, 3.5, 32, 8
+    L = 3.0
+    # xi so that eta = P L^2 xi^2 / (c^2 pi M^2) stays at 0.5 (Eq. 4.2)
+    xi = min(3.5, (0.5 * 0.95 ** 2 * np.pi * M * M / (P * L * L)) ** 0.5)
     # three calls in a row: the scratch keeps the previous call's contents,
     # so a repeated input and a new input must both come out right
     for seed in (3, 3, 4):
-        x, q = systems.uniform_charges(2000, L, seed=seed)
-        N = len(q)
+        x, q = systems.uniform_charges(N, L, seed=seed + M)
         xd = torch.tensor(x, device="cuda")
         qd = torch.tensor(q, device="cuda")
         H = torch.full((M, M, M), float("nan"), dtype=torch.float64, device="cuda")
@@ -57,16 +66,3 @@ def test_spread_noalloc_matches_plan_spread():
         assert torch.isfinite(H).all()
         assert _rel(H, Href) < TOL_FP64
         plan.close()
-
-
-def test_spread_noalloc_rejects_sizes_beyond_its_scratch():
-    import __graft_entry__
-    __graft_entry__.build()
-    torch.cuda.set_device(0)
-    lib = nat.load()
-    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    xd = torch.zeros((4, 3), dtype=torch.float64, device="cuda")
-    qd = torch.zeros(4, dtype=torch.float64, device="cuda")
-    H = torch.zeros(8, dtype=torch.float64, device="cuda")
-    assert lib.se_spread_noalloc(_p(xd), _p(qd), 32769, 3.0, 3.5, 32, 8, _p(H), stream) == nat.SE_ERR_ARG
-    assert lib.se_spread_noalloc(_p(xd), _p(qd), 4, 30.0, 0.5, 129, 8, _p(H), stream) == nat.SE_ERR_ARG
