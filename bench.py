@@ -610,7 +610,9 @@ def autograd_timing(se, torch, x, q, w, prec, plan, xd, qd, K, flush):
     """The differentiable energy (autograd.se_energy): forward alone (spread
     and scaling, energy from the grid) and forward + backward (the adjoint
     gather: dE/dx, dE/dq), each step launched from Python through
-    torch.autograd, timed with CUDA events around the step."""
+    torch.autograd (eager: the autograd engine's host time is part of it),
+    and the forward + backward replayed as one captured CUDA graph; timed
+    with CUDA events around the step."""
     from paper_1712_04718_gb300.autograd import se_energy
     xg = xd.clone().requires_grad_(True)
     qg = qd.clone().requires_grad_(True)
@@ -628,6 +630,22 @@ def autograd_timing(se, torch, x, q, w, prec, plan, xd, qd, K, flush):
     for name, fn in (("forward", fwd), ("forward_backward", fwd_bwd)):
         ms, k, _ = time_steps(torch, fn, K, 5, flush)
         res[name] = r4(k / (ms / 1e3))
+    # the same forward + backward captured in one CUDA graph (static inputs),
+    # the way a training step hides the autograd engine's host time
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            fwd_bwd()
+    torch.cuda.current_stream().wait_stream(s)
+    xg.grad = None
+    qg.grad = None
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="thread_local"):
+        se_energy(xg, qg, plan).backward()
+    ms, k, _ = time_steps(torch, g.replay, K, 5, flush)
+    res["forward_backward_graph"] = r4(k / (ms / 1e3))
+    del g
     res["unit"] = "evals/s"
     return res
 

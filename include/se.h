@@ -99,7 +99,13 @@ int se_plan_set_stream(se_plan *plan, void *stream);
  * with the scaling fused into the x pass, kernels chained by programmatic
  * dependent launch; 4 = the same pipeline with the particles left unsorted:
  * one kernel adds every weight into a float grid with global reductions
- * (the last bits of the grid then depend on the order of the additions).
+ * (the last bits of the grid then depend on the order of the additions);
+ * 5 = the pipeline of 3 with the inverse transform fused with the gather:
+ * each x-slab's real plane stays in shared memory, every particle takes its
+ * share of each plane of its support there, and a last kernel adds the P
+ * shares in a fixed order (the real grid is written only when se_copy_grid
+ * asks for it); SE_ERR_UNSUPPORTED where its shared memory (about
+ * 15 M^2 bytes) does not fit one CTA of the device (M = 128 on GB300).
  * tile = edge of a spreading tile in grid cells (0 = automatic, else
  * 2..32; for P <= 16 edges above 16 are reduced to 16, the largest the
  * staged tile regions' fixed row stride holds).  For benchmarking and

@@ -558,7 +558,7 @@ template <int P, int DD = pick_d(P)>
 struct TilePrep {
     static constexpr int D = DD;
     float gy[P], dgy[P], gz[D], dgz[D];
-    float ux, px0, Bx, q;
+    float ux, uy, px0, Bx, q;
     int base;   // region offset of support point (0, 0, this lane's first z)
 };
 
@@ -574,6 +574,7 @@ __device__ __forceinline__ void tile_prep(const f4& v, const KParams<float>& kp,
     const int cz = cell_of(v.z, kp.invh, kp.M, &t);
     const float uz = centre_offset(t, cz);
     fgg<float, P>(uy, kp.beta, kp.E3, g.gy);
+    g.uy = uy;
 #pragma unroll
     for (int b = 0; b < P; ++b) g.dgy[b] = (float(b) - 0.5f * float(P - 1) - uy) * g.gy[b];
 #pragma unroll
@@ -1390,6 +1391,366 @@ k_slab_inv_cl(const float2* __restrict__ Cg, float* __restrict__ R, const float2
         dst[e] = S[yl * SP + z];
     }
     SE_STAMP(5, 4);
+}
+#endif  // SE_BATCH_TU
+
+// ---------------------------------------------------------------------------
+// Variant 5: the inverse slab transform fused with the gather (Eq. 3.9 and
+// the analytic force of Sec. 3.1).  The 2-CTA cluster of x-slab x transforms
+// the slab back to real space as k_slab_inv_cl does, but keeps the real
+// plane Ht[x][y][z] in shared memory (each CTA sends the rows it produced to
+// its partner, so both hold the whole plane) instead of writing the grid.
+// Then every particle whose support contains plane x, i.e. x = i0x + a with
+// 0 <= a < P, takes its sums over that plane,
+//   S0 = sum_{b,c} gy_b gz_c Ht,  Sy = sum dgy_b gz_c Ht,  Sz = sum gy_b dgz_c Ht,
+// and stores the plane's share of its potential and force sums as one
+// float4 (gx_a S0, dgx_a S0, gx_a Sy, gx_a Sz) at part[a][particle].  Each
+// (particle, a) pair is written by exactly one CTA: the particles come from
+// the tile buckets of the columns of tiles holding the cells x - P/2 .. x +
+// P/2 - 1, split between the two CTAs by tile, and from the overflow list,
+// split over all warps of the cluster.  k_gfinish then adds the P shares of
+// each particle in the order a = 0 .. P-1: the result does not depend on
+// how the work was scheduled.  The grid is read from shared memory instead
+// of L2, and the real grid is never written.
+
+// shared memory: the inverse transform's regions (slabcl_layout) | the real
+// plane, M rows sg_row_stride(M) floats apart
+__host__ __device__ inline int sg_row_stride(int M) { return M + 1; }
+__host__ __device__ inline size_t sg_plane_offset(int M) { return (slabcl_layout(M).total + 15) / 16 * 16; }
+__host__ __device__ inline size_t sg_smem_bytes(int M) {
+    return sg_plane_offset(M) + (size_t)M * sg_row_stride(M) * sizeof(float);
+}
+
+__device__ __forceinline__ f4 make_f4_zero() {
+    f4 v;
+    v.x = v.y = v.z = v.w = 0.0f;
+    return v;
+}
+
+// One particle's share of plane x, by the G lanes of its group (lane k: z
+// points k, k + G, ...); returns false (and zeros) when plane x is not in its
+// support.  a: the support index of plane x.
+template <int P, bool kForces>
+__device__ __forceinline__ bool plane_sums(const f4& v, const KParams<float>& kp, int x,
+                                           const float* __restrict__ PL, int SPL, int k, int* a_out,
+                                           float4* out) {
+    constexpr int D = pick_d(P), G = P / D;
+    const int M = kp.M;
+    float t;
+    const int cx = cell_of(v.x, kp.invh, M, &t);
+    int a = x - (cx - P / 2 + 1);
+    a = a < 0 ? a + M : (a >= M ? a - M : a);
+    *a_out = a;
+    if (a >= P) {
+        *out = make_float4(0.f, 0.f, 0.f, 0.f);
+        return false;
+    }
+    const float ux = centre_offset(t, cx);
+    const int cy = cell_of(v.y, kp.invh, M, &t);
+    const float uy = centre_offset(t, cy);
+    const int cz = cell_of(v.z, kp.invh, M, &t);
+    const float uz = centre_offset(t, cz);
+    float gy[P];
+    fgg<float, P>(uy, kp.beta, kp.E3, gy);
+    float gz[D], dgz[D];
+    int jz[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const int c = k + j * G;
+        const float dz = float(c) - 0.5f * float(P - 1) - uz;
+        gz[j] = expf(-kp.beta * dz * dz);
+        dgz[j] = dz * gz[j];
+        jz[j] = wrap_index(cz - P / 2 + 1 + c, M);
+    }
+    float tb0[D], tby[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) tb0[j] = tby[j] = 0.0f;
+    const int i0y = cy - P / 2 + 1;
+#pragma unroll
+    for (int b = 0; b < P; ++b) {
+        const float* row = PL + wrap_index(i0y + b, M) * SPL;
+        const float dgyb = (float(b) - 0.5f * float(P - 1) - uy) * gy[b];
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            const float hv = row[jz[j]];
+            tb0[j] += gy[b] * hv;
+            if constexpr (kForces) tby[j] += dgyb * hv;
+        }
+    }
+    float s0 = 0.0f, sy = 0.0f, sz = 0.0f;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        s0 += gz[j] * tb0[j];
+        if constexpr (kForces) {
+            sy += gz[j] * tby[j];
+            sz += dgz[j] * tb0[j];
+        }
+    }
+    // x factor of support point a (the exponent written about the support
+    // centre, as in fgg)
+    const float gxa = expf(-kp.beta * ux * (ux + float(P - 1)) + 2.0f * kp.beta * ux * float(a)) *
+                      kp.E3[a];
+    const float dgxa = (float(a) - 0.5f * float(P - 1) - ux) * gxa;
+    *out = make_float4(gxa * s0, dgxa * s0, gxa * sy, gxa * sz);
+    return true;
+}
+
+// Sum of a float4 over the G lanes of a group (the whole warp takes part),
+// valid in lane k = 0 of the group.
+template <int G>
+__device__ __forceinline__ float4 group_sum4(float4 v, int k) {
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) {
+        const float a0 = __shfl_down_sync(0xffffffffu, v.x, o);
+        const float a1 = __shfl_down_sync(0xffffffffu, v.y, o);
+        const float a2 = __shfl_down_sync(0xffffffffu, v.z, o);
+        const float a3 = __shfl_down_sync(0xffffffffu, v.w, o);
+        if (k + o < G) {
+            v.x += a0;
+            v.y += a1;
+            v.z += a2;
+            v.w += a3;
+        }
+    }
+    return v;
+}
+
+#ifndef SE_BATCH_TU
+// Clusters 0..M-1: slab x = cluster index; cluster M: the grid energy from
+// the x pass's nparts partials (acc->e_grid and, scaled, *E_grid).
+// forces = 0: potential sums only (the force entries of part are zero).
+template <int P, bool kForces>
+__global__ void __launch_bounds__(kSlabThreads)
+k_sinv_gather_cl(const float2* __restrict__ Cg, const float2* __restrict__ tw_g, const KParams<float> kp,
+                 const double* __restrict__ xparts, int nparts, Acc* acc, double e_scale,
+                 double* E_grid, const f4* __restrict__ bucket, const int* __restrict__ bucket_idx,
+                 int cap, const int* __restrict__ tile_n, const int* __restrict__ over_idx,
+                 const f4* __restrict__ wrapped, float4* __restrict__ part) {
+    namespace cg = cooperative_groups;
+    constexpr int D = pick_d(P), G = P / D, GPW = 32 / G;
+    (void)D;
+    pdl_wait();
+    pdl_launch_next();
+    const int M = kp.M;
+    const int x = blockIdx.x / kSlabCL;
+    if (x == M) {   // the whole cluster takes this branch
+        if (blockIdx.x % kSlabCL != 0) return;
+        __shared__ df2 sbuf[32];
+        const df2 sum = sum_partials_df(reinterpret_cast<const float*>(xparts), nparts, 1, 0, sbuf);
+        if (threadIdx.x == 0) {
+            const double e = df_to_double(sum);
+            acc->e_grid = e;
+            if (E_grid) *E_grid = e_scale * e;
+        }
+        return;
+    }
+    extern __shared__ __align__(16) unsigned char sm[];
+    cg::cluster_group clu = cg::this_cluster();
+    const int rank = (int)clu.block_rank();
+    const SlabClLayout l = slabcl_layout(M);
+    const int Mh = M / 2 + 1, SP = M + 1, SPL = sg_row_stride(M);
+    float2* tw = reinterpret_cast<float2*>(sm + l.tw);
+    float2* A = reinterpret_cast<float2*>(sm + l.a);
+    float2* Z = reinterpret_cast<float2*>(sm + l.b);
+    float2* T = reinterpret_cast<float2*>(sm + l.c);
+    float2* X = reinterpret_cast<float2*>(sm + l.d);
+    float* PL = reinterpret_cast<float*>(sm + sg_plane_offset(M));
+    const int y0 = rank * l.ry, ny = max(0, min(l.ry, M - y0));
+    const int k0 = rank * l.kc, nk = max(0, min(l.kc, Mh - k0));
+    load_twiddles(tw, tw_g, M);
+    const FDiv fnk = fdiv_of(max(nk, 1)), fM = fdiv_of(M);
+    // own kz columns of the slab times the Hermitian weights (1 at kz = 0 and
+    // M/2, else 2): A[ky][kl]
+    const float2* src = Cg + (size_t)x * M * Mh + k0;
+    for (int e0 = threadIdx.x; e0 < M * nk; e0 += blockDim.x * kLoadBatch) {
+        float2 v[kLoadBatch];
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int e = e0 + u * (int)blockDim.x;
+            if (e < M * nk) {
+                const int ky = fdiv(e, fnk), kl = e - ky * nk;
+                v[u] = src[(size_t)ky * Mh + kl];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int e = e0 + u * (int)blockDim.x;
+            if (e < M * nk) {
+                const int ky = fdiv(e, fnk), kl = e - ky * nk;
+                const int kz = k0 + kl;
+                const float wgt = (kz == 0 || 2 * kz == M) ? 1.0f : 2.0f;
+                A[ky * l.kc + kl] = make_float2(wgt * v[u].x, wgt * v[u].y);
+            }
+        }
+    }
+    __syncthreads();
+    // y inverse: X(j = ky, c = kl) = A[ky][kl]  ->  T[kl][y]
+    dft_c2c_fact<kClInvTK, kClInvTC>(A, l.kc, 1, T, 1, SP, nk, Z, tw, M, 1.0f);
+    __syncthreads();
+    // push: row y of these kz columns goes to the CTA owning y
+    {
+        float2* Xr[kSlabCL];
+#pragma unroll
+        for (int r = 0; r < kSlabCL; ++r) Xr[r] = clu.map_shared_rank(X, r);
+        for (int e = threadIdx.x; e < nk * M; e += blockDim.x) {
+            const int kl = fdiv(e, fM), y = e - kl * M;
+            const int owner = y >= l.ry ? 1 : 0;
+            Xr[owner][(k0 + kl) * l.ry + (y - owner * l.ry)] = T[kl * SP + y];
+        }
+    }
+    clu.sync();   // every push has landed
+    // z complex to real, own rows, straight into the plane: PL[y0 + yl][z]
+    dft_c2r<kClInvTK, kClInvTC>(X, l.ry, 1, PL + (size_t)y0 * SPL, 1, SPL, Mh, M, ny, tw, M);
+    __syncthreads();
+    // own rows to the partner, so that both CTAs hold the whole plane
+    for (int r = 0; r < kSlabCL; ++r) {
+        if (r == rank) continue;
+        float* PLr = clu.map_shared_rank(PL, r);
+        for (int e = threadIdx.x; e < ny * M; e += blockDim.x) {
+            const int yl = fdiv(e, fM), z = e - yl * M;
+            const size_t o = (size_t)(y0 + yl) * SPL + z;
+            PLr[o] = PL[o];
+        }
+    }
+    clu.sync();   // the plane is complete in both CTAs; no remote access after this
+    // the shares of plane x: tiles of the columns holding cells x - P/2 ..
+    // x + P/2 - 1 (periodic), alternate tiles to the two CTAs, one tile per
+    // warp at a time, GPW particles of it per round
+    const int TT = kp.tile, nT = kp.nT, N = kp.N;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int gi = lane / G, k = lane - gi * G;
+    const bool act = gi < GPW;
+    const int c_first = wrap_index(x - P / 2, M);
+    const int tx_first = c_first / TT;
+    // tile columns tx_first, tx_first + 1, ... (mod nT) until the P cells are covered
+    int ncol = 0;
+    {
+        int last = -1;
+        for (int j = 0; j < P; ++j) {
+            const int tx = wrap_index(c_first + j, M) / TT;
+            if (tx != last) {
+                ++ncol;
+                last = tx;
+            }
+        }
+    }
+    const int nitems = ncol * nT * nT;
+    for (int it = rank + kSlabCL * warp; it < nitems; it += kSlabCL * nw) {
+        const int ci = it / (nT * nT), rem = it - ci * nT * nT;
+        int tx = tx_first + ci;
+        if (tx >= nT) tx -= nT;
+        // a column reached twice through the wrap (ncol > nT) is taken once
+        if (ci >= nT) continue;
+        const int tile = tx * nT * nT + rem;
+        const int n = min(tile_n[tile], cap);
+        for (int s0 = 0; s0 < n; s0 += GPW) {
+            const int s = s0 + gi;
+            const bool valid = act && s < n;
+            f4 v = make_f4_zero();
+            int orig = 0;
+            if (valid) {
+                v = bucket[(size_t)tile * cap + s];
+                orig = bucket_idx[(size_t)tile * cap + s];
+            }
+            int a = P;
+            float4 sh = make_float4(0.f, 0.f, 0.f, 0.f);
+            const bool in = valid && plane_sums<P, kForces>(v, kp, x, PL, SPL, k, &a, &sh);
+            sh = group_sum4<G>(sh, k);
+            if (in && k == 0) part[(size_t)a * N + orig] = sh;
+        }
+    }
+    // the overflow list, over all warps of the cluster
+    const int n_over = min(tile_n[kp.ntiles], N);
+    const int gwarp = rank * nw + warp, ngw = kSlabCL * nw;
+    for (int o0 = gwarp * GPW; o0 < n_over; o0 += ngw * GPW) {
+        const int o = o0 + gi;
+        const bool valid = act && o < n_over;
+        f4 v = make_f4_zero();
+        int orig = 0;
+        if (valid) {
+            orig = over_idx[o];
+            v = wrapped[orig];
+        }
+        int a = P;
+        float4 sh = make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool in = valid && plane_sums<P, kForces>(v, kp, x, PL, SPL, k, &a, &sh);
+        sh = group_sum4<G>(sh, k);
+        if (in && k == 0) part[(size_t)a * N + orig] = sh;
+    }
+}
+
+// The P shares of each particle added in the order a = 0 .. P-1 (input
+// order, one particle per thread): phi and F at the particle's input
+// position, the energy 1/2 sum q phi by a double-float last-block reduction
+// as in k_gather.  adj (device scalar, or null): the adjoint, phi and F
+// scaled to dl/dq = g phi and dl/dx = -g F.
+template <int P>
+__global__ void __launch_bounds__(256)
+k_gfinish(const float4* __restrict__ part, const f4* __restrict__ wrapped, float* __restrict__ phi,
+          float* __restrict__ F, const KParams<float> kp, double* __restrict__ partials,
+          unsigned* ticket, Acc* acc, double e_scale, double* E_out, const double* __restrict__ adj) {
+    __shared__ df2 sbuf[32];
+    pdl_wait();
+    pdl_launch_next();
+    const int N = kp.N;
+    const float gsc = adj ? (float)__ldg(adj) : 1.0f;
+    const float phi_mul = gsc, F_mul = adj ? -gsc : 1.0f;
+    df2 e_df = df_from(0.0f);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        float4 sh[P];
+#pragma unroll
+        for (int a = 0; a < P; ++a) sh[a] = __ldcg(part + (size_t)a * N + i);
+        float s0 = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+        for (int a = 0; a < P; ++a) {
+            s0 += sh[a].x;
+            sx += sh[a].y;
+            sy += sh[a].z;
+            sz += sh[a].w;
+        }
+        const float qq = wrapped[i].w;
+        const float ph = s0 * kp.phi_scale;
+        if (phi) phi[i] = ph * phi_mul;
+        if (F) {
+            const float fm = qq * kp.F_scale * F_mul;
+            F[3 * i] = fm * sx;
+            F[3 * i + 1] = fm * sy;
+            F[3 * i + 2] = fm * sz;
+        }
+        e_df = df_add(e_df, df_from(qq * ph));
+    }
+    float* pf = reinterpret_cast<float*>(partials);
+    const df2 r = block_sum_df(e_df, sbuf);
+    if (threadIdx.x == 0) {
+        pf[2 * blockIdx.x] = r.hi;
+        pf[2 * blockIdx.x + 1] = r.lo;
+    }
+    const bool lastb = last_block(ticket);
+    if (!lastb || threadIdx.x >= 32) return;
+    const df2 t = warp_sum_partials_df(pf, gridDim.x, 1, 0);
+    if (threadIdx.x == 0) {
+        const double sum = df_to_double(t);
+        acc->e_gather = sum;
+        if (E_out) *E_out = e_scale * sum;
+        *ticket = 0u;
+    }
+}
+
+// The grid energy alone (acc->e_grid and, scaled, *E_out) from the x pass's
+// nparts partials: one CTA, for an energy-only evaluation of variant 5 (its
+// full evaluation sums it in the extra cluster of k_sinv_gather_cl).
+__global__ void __launch_bounds__(256)
+k_grid_energy(const double* __restrict__ xparts, int nparts, Acc* acc, double e_scale,
+              double* E_out) {
+    __shared__ df2 sbuf[32];
+    pdl_wait();
+    pdl_launch_next();
+    const df2 sum = sum_partials_df(reinterpret_cast<const float*>(xparts), nparts, 1, 0, sbuf);
+    if (threadIdx.x == 0) {
+        const double e = df_to_double(sum);
+        acc->e_grid = e;
+        if (E_out) *E_out = e_scale * e;
+    }
 }
 #endif  // SE_BATCH_TU
 

@@ -103,9 +103,98 @@ cudaError_t fast_spread(const float* xyz, const float* q, const KParams<float>& 
     }
 }
 
+// 2-CTA clusters per x-slab when every CTA gets an SM of its own
+inline bool slab_clusters(int M) {
+    const int nsm = sm_count();
+    return nsm > 0 && kSlabCL * (M + 1) <= nsm;
+}
+
+cudaError_t fast_inverse(const KParams<float>& kp, const FastBufs& b, double e_scale,
+                         double* E_grid, cudaStream_t s) {
+    const int M = kp.M, Mh = M / 2 + 1;
+    const int nch = (Mh + kFastKC - 1) / kFastKC;
+    const float2* tw = (const float2*)b.tw;
+    const float2* C = (const float2*)b.cgrid;
+    const int nsm = sm_count();
+    cudaError_t e;
+    if (!slab_clusters(M)) {
+        const size_t slab = std::max(slab_smem_bytes(M), kSlabSmemFloor);
+        e = cudaFuncSetAttribute(k_slab_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab);
+        if (e != cudaSuccess) return e;
+        return launch_ex(k_slab_inv, M + 1, kSlabThreads, slab, s, true, C, b.rgrid, tw, M,
+                         (const double*)(b.partials + 5 * kMaxPartials), M * nch, b.acc, e_scale,
+                         E_grid);
+    }
+    const int per_sm = nsm > 0 ? (kSlabCL * (M + 1) + nsm - 1) / nsm : 1;
+    const size_t cl = smem_cap_per_sm(slabcl_layout(M).total, per_sm);
+    e = cudaFuncSetAttribute(k_slab_inv_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cl);
+    if (e != cudaSuccess) return e;
+    return launch_cluster(k_slab_inv_cl, kSlabCL * (M + 1), kSlabThreads, cl, kSlabCL, s, true, C,
+                          b.rgrid, tw, M, (const double*)(b.partials + 5 * kMaxPartials), M * nch,
+                          b.acc, e_scale, E_grid);
+}
+
+bool fast_slab_gather_ok(int M) {
+    int dev = 0, optin = 0;
+    if (M < 2 || M > kFastMaxM || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return false;
+    return sg_smem_bytes(M) <= (size_t)optin;
+}
+
+cudaError_t fast_grid_energy(const KParams<float>& kp, const FastBufs& b, double e_scale,
+                             double* E_out, cudaStream_t s) {
+    const int Mh = kp.M / 2 + 1;
+    const int nch = (Mh + kFastKC - 1) / kFastKC;
+    return launch_ex(k_grid_energy, 1, kThreads, 0, s, true,
+                     (const double*)(b.partials + 5 * kMaxPartials), kp.M * nch, b.acc, e_scale,
+                     E_out);
+}
+
+template <int P>
+cudaError_t fast_gather_slab_P(const KParams<float>& kp, const FastBufs& b, float* phi, float* F,
+                               double* partials, unsigned* ticket, double e_scale, double* E_out,
+                               const double* adj, cudaStream_t s) {
+    const int M = kp.M, Mh = M / 2 + 1;
+    const int nch = (Mh + kFastKC - 1) / kFastKC;
+    const int nsm = sm_count();
+    // at most ceil(2 (M + 1) / SMs) CTAs per SM, whatever else is resident
+    // when the grid is scheduled early
+    const int per_sm = nsm > 0 ? (kSlabCL * (M + 1) + nsm - 1) / nsm : 1;
+    const size_t cl = smem_cap_per_sm(sg_smem_bytes(M), per_sm);
+    const bool forces = F != nullptr || adj != nullptr;
+    void (*kern)(const float2*, const float2*, const KParams<float>, const double*, int, Acc*, double,
+                 double*, const f4*, const int*, int, const int*, const int*, const f4*, float4*) =
+        forces ? k_sinv_gather_cl<P, true> : k_sinv_gather_cl<P, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cl);
+    if (e != cudaSuccess) return e;
+    e = launch_cluster(kern, kSlabCL * (M + 1), kSlabThreads, cl, kSlabCL, s, true,
+                       (const float2*)b.cgrid, (const float2*)b.tw, kp,
+                       (const double*)(b.partials + 5 * kMaxPartials), M * nch, b.acc, 0.0,
+                       (double*)nullptr, (const f4*)b.bucket, (const int*)b.bucket_idx, b.cap,
+                       (const int*)b.tile_n, (const int*)b.over_idx, (const f4*)b.wrapped,
+                       (float4*)b.part);
+    if (e != cudaSuccess) return e;
+    const int blocks = std::max(1, std::min((kp.N + kThreads - 1) / kThreads, kMaxPartials));
+    return launch_ex(k_gfinish<P>, blocks, kThreads, 0, s, true, (const float4*)b.part,
+                     (const f4*)b.wrapped, phi, F, kp, partials, ticket, b.acc, e_scale, E_out, adj);
+}
+
+cudaError_t fast_gather_slab(const KParams<float>& kp, const FastBufs& b, float* phi, float* F,
+                             double* partials, unsigned* ticket, double e_scale, double* E_out,
+                             const double* adj, cudaStream_t s) {
+    switch (kp.P) {
+#define SE_CASE(PP) \
+    case PP: return fast_gather_slab_P<PP>(kp, b, phi, F, partials, ticket, e_scale, E_out, adj, s);
+        SE_FOR_EACH_P(SE_CASE)
+#undef SE_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t fast_transform(const KParams<float>& kp, const FastBufs& b, double e_scale,
                            double* E_grid, cudaStream_t s, bool marks, void (*mark)(void*, int),
-                           void* ctx) {
+                           void* ctx, bool inverse) {
     const int M = kp.M, Mh = M / 2 + 1;
     const int nch = (Mh + kFastKC - 1) / kFastKC;
     const float2* tw = (const float2*)b.tw;
@@ -146,21 +235,7 @@ cudaError_t fast_transform(const KParams<float>& kp, const FastBufs& b, double e
                   b.partials + 5 * kMaxPartials);
     if (e != cudaSuccess) return e;
     if (marks) mark(ctx, 4);
-    if (!clusters) {
-        e = cudaFuncSetAttribute(k_slab_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab);
-        if (e != cudaSuccess) return e;
-        e = launch_ex(k_slab_inv, M + 1, kSlabThreads, slab, s, true, (const float2*)C, b.rgrid, tw, M,
-                      (const double*)(b.partials + 5 * kMaxPartials), M * nch, b.acc, e_scale, E_grid);
-    } else {
-        const int per_sm = nsm > 0 ? (kSlabCL * (M + 1) + nsm - 1) / nsm : 1;
-        const size_t cl = smem_cap_per_sm(slabcl_layout(M).total, per_sm);
-        e = cudaFuncSetAttribute(k_slab_inv_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cl);
-        if (e != cudaSuccess) return e;
-        e = launch_cluster(k_slab_inv_cl, kSlabCL * (M + 1), kSlabThreads, cl, kSlabCL, s, true,
-                           (const float2*)C, b.rgrid, tw, M,
-                           (const double*)(b.partials + 5 * kMaxPartials), M * nch, b.acc, e_scale,
-                           E_grid);
-    }
+    if (inverse) e = fast_inverse(kp, b, e_scale, E_grid, s);
     if (e != cudaSuccess) return e;
     if (marks) mark(ctx, 5);
     return cudaSuccess;

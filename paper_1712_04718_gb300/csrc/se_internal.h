@@ -112,6 +112,7 @@ struct FastBufs {
                           // CTAs, [4] overflow count
     Acc* acc;
     bool unsorted;        // spread unsorted into a float grid (k_fdirect)
+    void* part;           // variant 5: float4 [P][N], each particle's share of each x-plane
 };
 cudaError_t fast_spread(const float* xyz, const float* q, const KParams<float>& kp,
                         const FastBufs& b, cudaStream_t s, bool marks, void (*mark)(void*, int),
@@ -120,9 +121,25 @@ bool fast_gather_tiled(const KParams<float>& kp);
 cudaError_t fast_gather(const KParams<float>& kp, const FastBufs& b, float* phi, float* F,
                         double* partials, unsigned* ticket, double e_scale, double* E_out,
                         const double* adj, cudaStream_t s);
+// forward transform, x pass (scaling, grid energy partials) and, with
+// inverse, the inverse transform into b.rgrid (variant 5 fuses the inverse
+// with its gather instead)
 cudaError_t fast_transform(const KParams<float>& kp, const FastBufs& b, double e_scale,
                            double* E_grid, cudaStream_t s, bool marks, void (*mark)(void*, int),
-                           void* ctx);
+                           void* ctx, bool inverse = true);
+// the inverse transform alone (the real grid of variant 5 on request)
+cudaError_t fast_inverse(const KParams<float>& kp, const FastBufs& b, double e_scale,
+                         double* E_grid, cudaStream_t s);
+// variant 5: the grid energy from the x pass's partials (energy only), and
+// the inverse transform fused with the gather, then the sum of the shares
+cudaError_t fast_grid_energy(const KParams<float>& kp, const FastBufs& b, double e_scale,
+                             double* E_out, cudaStream_t s);
+// whether variant 5's shared memory (the inverse transform's regions and
+// the real plane) fits one CTA on the current device for this M
+bool fast_slab_gather_ok(int M);
+cudaError_t fast_gather_slab(const KParams<float>& kp, const FastBufs& b, float* phi, float* F,
+                             double* partials, unsigned* ticket, double e_scale, double* E_out,
+                             const double* adj, cudaStream_t s);
 cudaError_t fast_to_real(const FastBufs& b, int M, float* dst, cudaStream_t s);
 cudaError_t launch_gather_pdl(const f4* sorted, const int* perm, const float* grid, float* phi,
                               float* F, const KParams<float>& kp, double* partials,

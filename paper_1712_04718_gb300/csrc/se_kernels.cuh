@@ -608,8 +608,8 @@ struct GatherPrep {
     static constexpr int D = pick_d(P);
     T gy[P], dgy[P], gz[D], dgz[D];
     int jy[P], jz[D];
-    T ux, px0, Bx;
-    int i0x;
+    T ux, uy, px0, Bx;
+    int i0x, i0y;
 };
 
 template <typename T, int P>
@@ -625,8 +625,10 @@ __device__ __forceinline__ void gather_prep(const v4_t<T>& v, const KParams<T>& 
     const int cz = cell_of(v.z, kp.invh, M, &t);
     const T uz = centre_offset(t, cz);
     fgg<T, P>(uy, kp.beta, kp.E3, g.gy);
+    g.uy = uy;
     g.i0x = cx - P / 2 + 1;
     const int i0y = cy - P / 2 + 1;
+    g.i0y = i0y;
 #pragma unroll
     for (int b = 0; b < P; ++b) {
         g.dgy[b] = (T(b) - T(0.5) * T(P - 1) - uy) * g.gy[b];
@@ -644,6 +646,10 @@ __device__ __forceinline__ void gather_prep(const v4_t<T>& v, const KParams<T>& 
     g.px0 = expT(-kp.beta * g.ux * (g.ux + T(P - 1)));
 }
 
+#ifndef SE_GATHER_UNROLL
+#define SE_GATHER_UNROLL 2
+#endif
+constexpr int kGatherUnroll = SE_GATHER_UNROLL;   // x planes in flight (single precision, P <= 8)
 template <typename T, int P>
 __device__ __forceinline__ void gather_accum(const GatherPrep<T, P>& g, const T* __restrict__ grid,
                                              const KParams<T>& kp, const T* sE3, T& vphi, T& vfx,
@@ -654,32 +660,65 @@ __device__ __forceinline__ void gather_accum(const GatherPrep<T, P>& g, const T*
 #pragma unroll
     for (int j = 0; j < D; ++j) acc0[j] = accx[j] = accy[j] = T(0);
     T px = g.px0;
-    // small supports: the whole x loop unrolled, so that every load of
-    // the particle's P^3 grid values is in flight at once
-#pragma unroll(P <= 8 ? P : 1)
-    for (int a = 0; a < P; ++a) {
-        const T gxa = px * sE3[a];
-        const T dgxa = (T(a) - T(0.5) * T(P - 1) - g.ux) * gxa;
-        px *= g.Bx;
-        const int jx = wrap_index(g.i0x + a, M);
-        T tb0[D], tby[D];
+    if constexpr (sizeof(T) == sizeof(float) && P <= 8) {
+        // single precision, small supports: kGatherUnroll x planes at a
+        // time, the rows' grid offsets formed in the loop instead of kept in
+        // P registers (with them, and all planes in flight, the accumulation
+        // exceeds the 64 registers of four CTAs per SM and spills)
+#pragma unroll(kGatherUnroll)
+        for (int a = 0; a < P; ++a) {
+            const T gxa = px * sE3[a];
+            const T dgxa = (T(a) - T(0.5) * T(P - 1) - g.ux) * gxa;
+            px *= g.Bx;
+            const T* plane = grid + (size_t)wrap_index(g.i0x + a, M) * M * M;
+            T tb0[D], tby[D];
 #pragma unroll
-        for (int j = 0; j < D; ++j) tb0[j] = tby[j] = T(0);
+            for (int j = 0; j < D; ++j) tb0[j] = tby[j] = T(0);
 #pragma unroll
-        for (int b = 0; b < P; ++b) {
-            const T* row = grid + ((size_t)jx * M + g.jy[b]) * M;
+            for (int b = 0; b < P; ++b) {
+                const T* row = plane + wrap_index(g.i0y + b, M) * M;
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    const T hv = __ldg(row + g.jz[j]);
+                    tb0[j] += g.gy[b] * hv;
+                    tby[j] += g.dgy[b] * hv;
+                }
+            }
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                const T hv = __ldg(row + g.jz[j]);
-                tb0[j] += g.gy[b] * hv;
-                tby[j] += g.dgy[b] * hv;
+                acc0[j] += gxa * tb0[j];
+                accx[j] += dgxa * tb0[j];
+                accy[j] += gxa * tby[j];
             }
         }
+    } else {
+        // the whole x loop unrolled for small supports, so that every load of
+        // the particle's P^3 grid values is in flight at once
+#pragma unroll(P <= 8 ? P : 1)
+        for (int a = 0; a < P; ++a) {
+            const T gxa = px * sE3[a];
+            const T dgxa = (T(a) - T(0.5) * T(P - 1) - g.ux) * gxa;
+            px *= g.Bx;
+            const int jx = wrap_index(g.i0x + a, M);
+            T tb0[D], tby[D];
 #pragma unroll
-        for (int j = 0; j < D; ++j) {
-            acc0[j] += gxa * tb0[j];
-            accx[j] += dgxa * tb0[j];
-            accy[j] += gxa * tby[j];
+            for (int j = 0; j < D; ++j) tb0[j] = tby[j] = T(0);
+#pragma unroll
+            for (int b = 0; b < P; ++b) {
+                const T* row = grid + ((size_t)jx * M + g.jy[b]) * M;
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    const T hv = __ldg(row + g.jz[j]);
+                    tb0[j] += g.gy[b] * hv;
+                    tby[j] += g.dgy[b] * hv;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                acc0[j] += gxa * tb0[j];
+                accx[j] += dgxa * tb0[j];
+                accy[j] += gxa * tby[j];
+            }
         }
     }
 #pragma unroll
@@ -692,7 +731,7 @@ __device__ __forceinline__ void gather_accum(const GatherPrep<T, P>& g, const T*
 }
 
 // Single precision and P <= 8: at most 64 registers, so that four CTAs fit on
-// an SM and a gather of up to 4 x 152 CTAs runs in one wave.
+// an SM (a bound of 48 for five makes the accumulation spill).
 template <typename T, int P>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 8) ? 4 : 1)
 k_gather(const v4_t<T>* __restrict__ sorted, const int* __restrict__ perm,

@@ -12,7 +12,9 @@
 //   k_gather (Eq. 3.9 and the analytic force; energy 1/2 sum q phi)
 // or the single-precision pipeline of se_fast.cuh (variant 3: k_fbin,
 // k_fspread, k_slab_fwd, k_xpass, k_slab_inv, k_gather; variant 4: k_fdirect
-// in place of the first two), and nothing else: no allocation, no memset, no
+// in place of the first two; variant 5: k_fbin, k_fspread, k_slab_fwd,
+// k_xpass, then k_sinv_gather_cl, the inverse transform fused with the
+// gather, and k_gfinish), and nothing else: no allocation, no memset, no
 // host synchronisation except the final copy of the energy when the caller
 // asks for it on the host.
 #include <cufft.h>
@@ -70,6 +72,7 @@ struct se_plan {
     void* bucket = nullptr;        // tile buckets (single-precision pipeline)
     int* bucket_idx = nullptr;     // their input positions
     long long* g64 = nullptr;      // fixed-point spread grid (single-precision pipeline)
+    void* part = nullptr;          // variant 5: float4 [P][N] shares of the x-planes
     float* green_f = nullptr;      // G(k) table in float (single-precision pipeline)
     void* tw = nullptr;            // twiddles of the single-precision pipeline
     double* partials = nullptr;    // 8 x kMaxPartials
@@ -183,7 +186,7 @@ void derive(se_plan* p) {
     p->ntiles = p->nT * p->nT * p->nT;
     const bool fast_ok = p->prec != SE_FP64 && p->M <= se::kFastMaxM;
     int variant = p->tune_variant;
-    if (variant == 3 && !fast_ok) variant = 0;
+    if ((variant == 3 || variant == 5) && !fast_ok) variant = 0;
     if (variant == 4 && (p->prec == SE_FP64 || p->M > se::kFastMaxM)) variant = 0;
     // ik forces need the three extra inverse transforms of the cuFFT pipeline
     if (p->force_mode == SE_FORCE_IK && variant >= 3) variant = 0;
@@ -220,12 +223,13 @@ void release_device(se_plan* p) {
     void* bufs[] = {p->grid_spread, p->grid_gather, p->cgrid, p->green, p->tile_count,
                     p->tile_start, p->slot, p->tile_of, p->perm, p->sorted, p->partials,
                     p->tickets, p->acc, p->dE, p->h_xyz, p->h_q, p->h_F, p->h_phi, p->g64, p->tw, p->green_f,
-                    p->bucket, p->bucket_idx, p->cgrid_ik};
+                    p->bucket, p->bucket_idx, p->cgrid_ik, p->part};
     for (void* b : bufs)
         if (b) cudaFree(b);
     p->grid_spread = p->grid_gather = p->cgrid = p->sorted = p->tw = p->bucket = nullptr;
     p->bucket_idx = nullptr;
     p->cgrid_ik = nullptr;
+    p->part = nullptr;
     p->g64 = nullptr;
     p->green_f = nullptr;
     p->green = p->partials = p->dE = nullptr;
@@ -309,10 +313,13 @@ int prepare(se_plan* p) {
     int rc = SE_OK;
     if (rc == SE_OK && !fast) rc = dalloc(&p->grid_spread, M3 * ts);
     if (rc == SE_OK && fast) rc = dalloc((void**)&p->g64, M3 * sizeof(long long));
-    if (rc == SE_OK && p->variant == 3)
+    const bool buckets = p->variant == 3 || p->variant == 5;
+    if (rc == SE_OK && buckets)
         rc = dalloc(&p->bucket, (size_t)p->ntiles * p->cap * 4 * sizeof(float));
-    if (rc == SE_OK && p->variant == 3)
+    if (rc == SE_OK && buckets)
         rc = dalloc((void**)&p->bucket_idx, (size_t)p->ntiles * p->cap * sizeof(int));
+    if (rc == SE_OK && p->variant == 5)
+        rc = dalloc(&p->part, N * (size_t)p->P * 4 * sizeof(float));
     if (rc == SE_OK && fast) rc = dalloc(&p->tw, (size_t)p->M * 2 * sizeof(float));
     if (rc == SE_OK && fast) rc = dalloc((void**)&p->green_f, nc * sizeof(float));
     if (rc == SE_OK) rc = dalloc(&p->grid_gather, ik ? 4 * ik_gstride(p) * ts : M3 * ts);
@@ -417,6 +424,7 @@ se::FastBufs fast_bufs(se_plan* p) {
     b.tickets = p->tickets;
     b.acc = p->acc;
     b.unsorted = p->variant == 4;
+    b.part = p->part;
     return b;
 }
 
@@ -443,8 +451,12 @@ int fast_scale(se_plan* p, double* E_grid) {
     const KParams<float> kp = make_kparams<float>(p);
     const double M3 = (double)p->M * p->M * p->M;
     const double e_scale = p->kc * p->h * p->h * p->h / (2.0 * M3);
+    // variant 5 runs the inverse transform inside its gather; the grid energy
+    // is summed here only when it is asked for
+    const bool v5 = p->variant == 5;
     SE_CUDA(se::fast_transform(kp, fast_bufs(p), e_scale, E_grid, p->stream, p->ev_cur >= 0,
-                               mark_cb, p));
+                               mark_cb, p, !v5));
+    if (v5 && E_grid) SE_CUDA(se::fast_grid_energy(kp, fast_bufs(p), e_scale, E_grid, p->stream));
     p->spread_clean = true;
     p->have_scale = true;
     return SE_OK;
@@ -452,6 +464,13 @@ int fast_scale(se_plan* p, double* E_grid) {
 
 int fast_gather(se_plan* p, void* phi, void* F, double* E, const double* adj = nullptr) {
     const KParams<float> kp = make_kparams<float>(p);
+    if (p->variant == 5) {   // the inverse transform fused with the gather
+        SE_CUDA(se::fast_gather_slab(kp, fast_bufs(p), (float*)phi, (float*)F,
+                                     p->partials + 4 * se::kMaxPartials, p->tickets + 2, 0.5, E,
+                                     adj, p->stream));
+        timing_mark(p, 6);
+        return SE_OK;
+    }
     // dense tiles: the tile gather, with or without forces (it stages the
     // grid once per tile, which outweighs the force sums it then skips)
     if (p->variant == 3 && se::fast_gather_tiled(kp)) {
@@ -782,10 +801,11 @@ int se_plan_set_stream(se_plan* p, void* stream) {
 }
 
 int se_plan_set_tuning(se_plan* p, int spread_variant, int tile) {
-    if (!p || spread_variant < 0 || spread_variant > 4 || (tile != 0 && (tile < 2 || tile > 32)))
+    if (!p || spread_variant < 0 || spread_variant > 5 || (tile != 0 && (tile < 2 || tile > 32)))
         return SE_ERR_ARG;
     if (spread_variant >= 3 && (p->prec == SE_FP64 || p->M > se::kFastMaxM)) return SE_ERR_UNSUPPORTED;
     if (spread_variant == 2 && p->prec == SE_FP32) return SE_ERR_UNSUPPORTED;
+    if (spread_variant == 5 && !se::fast_slab_gather_ok(p->M)) return SE_ERR_UNSUPPORTED;
     p->tune_variant = spread_variant;
     p->tune_tile = tile;
     invalidate(p);
@@ -918,8 +938,13 @@ int se_copy_grid(se_plan* p, int which, void* dst) {
     // the single-precision pipelines clear the spread grid in the transform:
     // it is there only between se_spread and se_scale
     if (which == 0 && p->variant >= 3 && p->spread_clean) return SE_ERR_ARG;
-    if (which == 0 && p->variant == 3)
+    if (which == 0 && (p->variant == 3 || p->variant == 5))
         return check_cuda(se::fast_to_real(fast_bufs(p), p->M, (float*)dst, p->stream));
+    if (which == 1 && p->variant == 5) {
+        // variant 5 keeps the real grid on chip: transform it back on request
+        if (!p->have_scale) return SE_ERR_ARG;
+        SE_CUDA(se::fast_inverse(make_kparams<float>(p), fast_bufs(p), 0.0, nullptr, p->stream));
+    }
     if (which == 0 && p->variant == 4) {
         SE_CUDA(cudaMemcpyAsync(dst, p->g64, bytes, cudaMemcpyDeviceToDevice, p->stream));
         return SE_OK;

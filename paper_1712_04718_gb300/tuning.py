@@ -1,10 +1,11 @@
 """Autotuning of the spreading variant and tile edge, with a JSON cache.
 
 For a single system the choice is between the sorted single-precision
-pipeline (variant 3) with a tile edge, which trades the particles each
-spreading block handles (and its shared-memory region) against the number of
-blocks and the region flushes, and the unsorted one (variant 4), which skips
-the sort and adds straight into the grid with global reductions.  The best
+pipeline with a tile edge, which trades the particles each spreading block
+handles (and its shared-memory region) against the number of blocks and the
+region flushes, with its own gather (variant 3) or with the gather fused into
+the inverse transform (variant 5), and the unsorted one (variant 4), which
+skips the sort and adds straight into the grid with global reductions.  The best
 choice depends on the grid, the support, the particle count and the GPU.
 tune_plan / tune_batch time a few candidates with CUDA events on the caller's
 inputs and remember the winner in a JSON file (SE_TUNE_CACHE, else
@@ -64,10 +65,12 @@ def _time(fn, reps):
 
 def default_configs(plan, unsorted=False):
     """(spread variant, tile edge) candidates for a plan: the sorted
-    single-precision pipeline's tile edges (and, with unsorted=True, the
-    unsorted variant 4 too)."""
+    single-precision pipeline's tile edges, with its own gather (variant 3)
+    and with the gather fused into the inverse transform (variant 5), and,
+    with unsorted=True, the unsorted variant 4 too."""
     if plan.prec != 0 and plan.M <= 128:
-        return ((4, 0),) * bool(unsorted) + tuple((3, t) for t in DEFAULT_CANDIDATES)
+        return ((4, 0),) * bool(unsorted) + tuple((v, t) for v in (3, 5)
+                                                  for t in DEFAULT_CANDIDATES)
     return tuple((0, t) for t in DEFAULT_CANDIDATES)
 
 
@@ -75,7 +78,7 @@ def tune_plan(plan, xyz, q, configs=None, reps=50, use_cache=True):
     """Pick the spread variant and tile edge of a single-system plan and set
     them; returns (variant, tile, ms, cached)."""
     configs = tuple(configs) if configs is not None else default_configs(plan)
-    key = "plan2:P%d:M%d:N%dk:prec%d:%s:%s" % (plan.P, plan.M, plan.N // 1000, plan.prec, _gpu(),
+    key = "plan3:P%d:M%d:N%dk:prec%d:%s:%s" % (plan.P, plan.M, plan.N // 1000, plan.prec, _gpu(),
                                               "-".join("%d.%d" % c for c in configs))
     if use_cache:
         hit = _load().get(key)

@@ -91,6 +91,7 @@ def test_ik_water_workload_more_accurate():
 
 
 @pytest.mark.parametrize("prec,variant", [("fp64", 0), ("fp64", 2), ("fp32", 0), ("fp32", 1),
+                                          ("fp32", 5),
                                           ("fp32", 4), ("fp32plain", 0)])
 def test_potential_only(prec, variant):
     """F = NULL selects the gather with the plain window: phi and E equal the
@@ -109,7 +110,8 @@ def test_potential_only(prec, variant):
     assert abs(E_p - E_f) < TOL[prec] * abs(E_f)
 
 
-@pytest.mark.parametrize("prec,variant", [("fp64", 0), ("fp32", 0), ("fp32", 1), ("fp32", 4)])
+@pytest.mark.parametrize("prec,variant", [("fp64", 0), ("fp32", 0), ("fp32", 1), ("fp32", 4),
+                                          ("fp32", 5)])
 def test_energy_only(prec, variant):
     """F = phi = NULL skips the gather: E is the grid energy
     kc h^3/(2 M^3) sum_k G |Hhat_k|^2, equal to the oracle's E_grid and to

@@ -75,6 +75,9 @@ SMALL = [  # (M, P, tile, variant): ragged tiles, P = M, large support, small ti
     (20, 8, 8, 0), (16, 4, 8, 0), (18, 10, 8, 0), (24, 12, 4, 0), (12, 12, 8, 0),
     (32, 16, 8, 0), (10, 2, 4, 0), (28, 6, 5, 0), (25, 8, 8, 0), (21, 6, 8, 0),
     (20, 8, 8, 1), (28, 6, 5, 1), (25, 8, 8, 1),
+    # 5: the gather fused into the inverse transform (single precision only)
+    (20, 8, 8, 5), (16, 4, 8, 5), (18, 10, 8, 5), (24, 12, 4, 5), (12, 12, 8, 5),
+    (32, 16, 8, 5), (10, 2, 4, 5), (28, 6, 5, 5), (25, 8, 8, 5), (21, 6, 8, 5),
 ]
 
 
@@ -87,7 +90,9 @@ def test_stage_parity_small(prec, M, P, tile, variant):
     xi = min(4.0, math.sqrt(0.8 * 0.95 ** 2 * math.pi * M * M / (P * L * L)))
     dtype = np.float64 if prec == "fp64" else np.float32
     x, q = systems.uniform_charges(301, L, seed=M * 100 + P, dtype=dtype)
-    if prec == "fp32plain" and tile == 5:
+    if prec == "fp64" and variant == 5:
+        pytest.skip("variant 5 is a single-precision pipeline")
+    if prec == "fp32plain" and tile == 5 and variant != 5:
         variant = 2     # uncompensated single precision may also spread directly
     q = q.astype(np.float64)
     q[-1] = -q[:-1].sum()   # neutral with an odd count
@@ -412,7 +417,7 @@ def test_unsorted_spread_water_workload():
     assert abs(g["E"] - r["E"]) < 5 * TOL["fp32"] * abs(r["E"])
 
 
-@pytest.mark.parametrize("variant", [3, 4])
+@pytest.mark.parametrize("variant", [3, 4, 5])
 def test_crowded_tile_overflow(variant):
     """600 of 800 charges inside one spreading tile: the tile's bucket fills
     and the rest take the overflow path (global fixed-point atomics).  Against
@@ -503,7 +508,7 @@ def test_sorted_spread_is_order_independent_and_grid_lifecycle():
     plan.close()
 
 
-@pytest.mark.parametrize("variant", [3, 4])
+@pytest.mark.parametrize("variant", [3, 4, 5])
 def test_empty_system_single_precision(variant):
     plan = se.Plan(0, 2.0, 4.0, 16, 4, precision="fp32", spread_variant=variant)
     xd = torch.empty((0, 3), dtype=torch.float32, device="cuda")
@@ -583,3 +588,61 @@ def test_random_configurations_single_precision(cfg):
     assert dF < 5 * TOL["fp32"] * scale, cfg
     assert_close(g["phi"], r["phi"], 5 * TOL["fp32"], label=cfg)
     assert abs(g["E"] - r["E"]) < 5 * TOL["fp32"] * abs(r["E"]) + 1e-12, cfg
+
+
+@pytest.mark.parametrize("P", [8, 12, 16])
+def test_single_precision_floor_water_box(P):
+    """The single-precision pipeline's own rounding floor on the 21 642-atom
+    water box (M = 52): its forces against the FP64 pipeline's on the same
+    positions, as the support grows (more terms per grid point and per
+    particle, with the fixed-point spread's per-weight quantum of
+    n 2^-30 c_g max|q|).  The floor stays far below the approximation error
+    of the method at these P (2.3e-4 at P = 8), so single precision does not
+    limit the accuracy the workloads state."""
+    x, q, w = systems.make("water-L6-M52-P8-fp32comp")
+    g32 = run_gpu(x, q, w["L"], w["xi"], w["M"], P, "fp32")
+    g64 = run_gpu(np.asarray(x, np.float64), np.asarray(q, np.float64), w["L"], w["xi"], w["M"],
+                  P, "fp64")
+    nw, elem = assert_close(g32["F"], g64["F"], 5 * TOL["fp32"], q=q, label="F fp32-fp64 P%d" % P)
+    assert nw < 1e-5, nw
+    assert_close(g32["phi"], g64["phi"], 5 * TOL["fp32"], label="phi fp32-fp64 P%d" % P)
+
+
+@pytest.mark.parametrize("variant,tile", [(3, 6), (5, 4), (5, 6), (5, 8)])
+def test_water_box_P8_every_particle(variant, tile):
+    """The 21 642-atom water box at P = 8 through both sorted single-precision
+    pipelines and several tile edges: every particle against O2, and the
+    fused gather (variant 5) bitwise repeatable from run to run."""
+    x, q, w = systems.make("water-L6-M52-P8-fp32comp")
+    N = len(q)
+    plan = se.Plan(N, w["L"], w["xi"], w["M"], w["P"], precision="fp32", spread_variant=variant,
+                   tile=tile)
+    xd = torch.tensor(x, device="cuda")
+    qd = torch.tensor(q, device="cuda")
+    E, F, phi = plan.energy_force(xd, qd)
+    F1, phi1 = F.clone(), phi.clone()
+    E2, F2, phi2 = plan.energy_force(xd, qd)
+    assert torch.equal(F1, F2) and torch.equal(phi1, phi2) and E == E2
+    r = oracle_for(np.asarray(x, np.float64), np.asarray(q, np.float64), w["L"], w["xi"], w["M"],
+                   w["P"], "fp32")
+    assert_close(F1.double().cpu().numpy(), r["F"], 5 * TOL["fp32"], q=q, label="F")
+    assert_close(phi1.double().cpu().numpy(), r["phi"], 5 * TOL["fp32"], label="phi")
+    assert abs(E - r["E"]) < 5 * TOL["fp32"] * abs(r["E"])
+    plan.close()
+
+
+def test_fused_gather_is_order_independent():
+    """Variant 5: each particle's share of each plane depends only on the
+    particle and the grid, and the shares are added in a fixed order, so
+    permuting the input permutes phi and F bitwise."""
+    L, xi, M, P = 2.0, 4.0, 24, 6
+    x, q = systems.uniform_charges(700, L, seed=71, dtype=np.float32)
+    perm = np.random.default_rng(74).permutation(700)
+    plan = se.Plan(700, L, xi, M, P, precision="fp32", spread_variant=5, tile=6)
+    _, F0, phi0 = plan.energy_force(torch.tensor(x, device="cuda"), torch.tensor(q, device="cuda"))
+    F0, phi0 = F0.cpu().numpy(), phi0.cpu().numpy()
+    _, F1, phi1 = plan.energy_force(torch.tensor(x[perm], device="cuda"),
+                                    torch.tensor(q[perm], device="cuda"))
+    assert np.array_equal(F1.cpu().numpy(), F0[perm])
+    assert np.array_equal(phi1.cpu().numpy(), phi0[perm])
+    plan.close()
