@@ -57,7 +57,8 @@ def test_argument_validation(lib):
     assert rc == nat.SE_OK and h.value
     assert lib.se_plan_set_precision(h, 7) == nat.SE_ERR_ARG
     assert lib.se_plan_set_shape(h, 1.5, 1) == nat.SE_ERR_ARG        # eta >= 1
-    assert lib.se_plan_set_tuning(h, 5, 0) == nat.SE_ERR_ARG
+    assert lib.se_plan_set_tuning(h, 6, 0) == nat.SE_ERR_ARG
+    assert lib.se_plan_set_tuning(h, 5, 0) == nat.SE_ERR_UNSUPPORTED  # single precision only
     assert lib.se_plan_set_tuning(h, 3, 0) == nat.SE_ERR_UNSUPPORTED  # the FP32 pipeline, FP64 plan
     assert lib.se_plan_set_tuning(h, 4, 0) == nat.SE_ERR_UNSUPPORTED
     assert lib.se_plan_set_precision(h, nat.SE_FP32) == nat.SE_OK
