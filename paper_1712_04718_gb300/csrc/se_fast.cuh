@@ -40,6 +40,10 @@
 namespace se {
 
 constexpr int kFastKC = 8;        // spectrum columns per block in the y and x passes
+#ifndef SE_XPASS_KC
+#define SE_XPASS_KC 8
+#endif
+constexpr int kXpassKC = SE_XPASS_KC;   // kz columns per block of the single-system x pass
 constexpr int kLoadBatch = 8;     // global loads per thread issued together in the transforms
 
 // cudaLaunchKernelEx with programmatic stream serialization (pdl = true): the
@@ -1036,18 +1040,19 @@ k_slab_fwd_f(float* __restrict__ grid, float2* __restrict__ C, const float2* __r
 
 // x pass of work item `item` = (ky, kz chunk): forward DFT along x, scaling
 // by G/M^3 with the grid energy (returned, valid in thread 0), inverse DFT.
+template <int KC = kFastKC>
 __device__ __forceinline__ df2 xpass_body(float2* __restrict__ C, const float2* __restrict__ tw_g,
                                           const float* __restrict__ green, int M, float invM3,
                                           int item) {
     __shared__ float2 tw[kFastMaxM];
-    __shared__ float2 s[kFastMaxM * kFastKC];
-    __shared__ float2 s2[kFastMaxM * kFastKC];
-    __shared__ float2 s3[kFastMaxM * kFastKC];   // scratch of the factored DFTs
+    __shared__ float2 s[kFastMaxM * KC];
+    __shared__ float2 s2[kFastMaxM * KC];
+    __shared__ float2 s3[kFastMaxM * KC];   // scratch of the factored DFTs
     __shared__ df2 sbuf[32];
     const int Mh = M / 2 + 1;
-    const int nch = (Mh + kFastKC - 1) / kFastKC;
-    const int y = item / nch, c0 = (item % nch) * kFastKC;
-    const int nc = min(kFastKC, Mh - c0);
+    const int nch = (Mh + KC - 1) / KC;
+    const int y = item / nch, c0 = (item % nch) * KC;
+    const int nc = min(KC, Mh - c0);
     const FDiv fnc = fdiv_of(nc);
     load_twiddles(tw, tw_g, M);
     for (int e0 = threadIdx.x; e0 < M * nc; e0 += blockDim.x * kLoadBatch) {
@@ -1065,28 +1070,28 @@ __device__ __forceinline__ df2 xpass_body(float2* __restrict__ C, const float2* 
             const int e = e0 + u * (int)blockDim.x;
             if (e < M * nc) {
                 const int x = fdiv(e, fnc), kk = e - x * nc;
-                s[x * kFastKC + kk] = v[u];
+                s[x * KC + kk] = v[u];
             }
         }
     }
     __syncthreads();
     SE_STAMP(4, 2);
-    dft_c2c_fact<1, 2>(s, kFastKC, 1, s2, kFastKC, 1, nc, s3, tw, M, -1.0f);
+    dft_c2c_fact<1, 2>(s, KC, 1, s2, KC, 1, nc, s3, tw, M, -1.0f);
     __syncthreads();
     SE_STAMP(4, 3);
     df2 en = df_from(0.0f);   // double-float energy sum
     for (int e = threadIdx.x; e < M * nc; e += blockDim.x) {
         const int kx = fdiv(e, fnc), kk = e - kx * nc;
         const int kz = c0 + kk;
-        const float2 v = s2[kx * kFastKC + kk];
+        const float2 v = s2[kx * KC + kk];
         const float g = green[((size_t)kx * M + y) * Mh + kz];
         en = df_add(en, df_from(((kz == 0 || 2 * kz == M) ? 1.0f : 2.0f) * g *
                                 fmaf(v.x, v.x, v.y * v.y)));
         const float f = g * invM3;
-        s2[kx * kFastKC + kk] = make_float2(v.x * f, v.y * f);
+        s2[kx * KC + kk] = make_float2(v.x * f, v.y * f);
     }
     __syncthreads();
-    dft_c2c_fact<1, 2>(s2, kFastKC, 1, C + (size_t)y * Mh + c0, M * Mh, 1, nc, s3, tw, M, 1.0f);
+    dft_c2c_fact<1, 2>(s2, KC, 1, C + (size_t)y * Mh + c0, M * Mh, 1, nc, s3, tw, M, 1.0f);
     SE_STAMP(4, 4);
     return block_sum_df(en, sbuf);
 }
@@ -1101,7 +1106,7 @@ k_xpass(float2* __restrict__ C, const float2* __restrict__ tw_g, const float* __
     pdl_wait();
     pdl_launch_next();
     SE_STAMP(4, 1);
-    const df2 tot = xpass_body(C, tw_g, green, M, invM3, blockIdx.x);
+    const df2 tot = xpass_body<kXpassKC>(C, tw_g, green, M, invM3, blockIdx.x);
     float* pf = reinterpret_cast<float*>(partials);
     if (threadIdx.x == 0) {
         pf[2 * blockIdx.x] = tot.hi;
@@ -1200,7 +1205,10 @@ k_slab_inv(const float2* __restrict__ C, float* __restrict__ R, const float2* __
 // opposite order, with the Hermitian weights of the z real transform applied
 // when the spectrum is loaded.
 
-constexpr int kSlabCL = 2;
+#ifndef SE_SLAB_CL
+#define SE_SLAB_CL 2
+#endif
+constexpr int kSlabCL = SE_SLAB_CL;   // CTAs per x-slab cluster
 // register tiles of the half-slab transforms (outputs x columns per thread):
 // the forward one has too few outputs to give every thread a 2 x 2 tile;
 // the inverse measured faster with 2 x 2
@@ -1291,7 +1299,7 @@ k_slab_fwd_cl(long long* __restrict__ g64, float2* __restrict__ Cg,
         const FDiv fny = fdiv_of(max(ny, 1));
         for (int e = threadIdx.x; e < Mh * ny; e += blockDim.x) {
             const int kz = fdiv(e, fny), yl = e - kz * ny;
-            const int owner = kz >= l.kc ? 1 : 0;
+            const int owner = min(kz / l.kc, kSlabCL - 1);
             Xr[owner][(kz - owner * l.kc) * M + y0 + yl] = T[kz * l.ry + yl];
         }
     }
@@ -1376,7 +1384,7 @@ k_slab_inv_cl(const float2* __restrict__ Cg, float* __restrict__ R, const float2
         for (int r = 0; r < kSlabCL; ++r) Xr[r] = clu.map_shared_rank(X, r);
         for (int e = threadIdx.x; e < nk * M; e += blockDim.x) {
             const int kl = fdiv(e, fM), y = e - kl * M;
-            const int owner = y >= l.ry ? 1 : 0;
+            const int owner = min(y / l.ry, kSlabCL - 1);
             Xr[owner][(k0 + kl) * l.ry + (y - owner * l.ry)] = T[kl * SP + y];
         }
     }
@@ -1594,7 +1602,7 @@ k_sinv_gather_cl(const float2* __restrict__ Cg, const float2* __restrict__ tw_g,
         for (int r = 0; r < kSlabCL; ++r) Xr[r] = clu.map_shared_rank(X, r);
         for (int e = threadIdx.x; e < nk * M; e += blockDim.x) {
             const int kl = fdiv(e, fM), y = e - kl * M;
-            const int owner = y >= l.ry ? 1 : 0;
+            const int owner = min(y / l.ry, kSlabCL - 1);
             Xr[owner][(k0 + kl) * l.ry + (y - owner * l.ry)] = T[kl * SP + y];
         }
     }

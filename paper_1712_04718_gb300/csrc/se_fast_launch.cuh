@@ -106,13 +106,13 @@ cudaError_t fast_spread(const float* xyz, const float* q, const KParams<float>& 
 // 2-CTA clusters per x-slab when every CTA gets an SM of its own
 inline bool slab_clusters(int M) {
     const int nsm = sm_count();
-    return nsm > 0 && kSlabCL * (M + 1) <= nsm;
+    return nsm > 0 && 2 * (M + 1) <= nsm;
 }
 
 cudaError_t fast_inverse(const KParams<float>& kp, const FastBufs& b, double e_scale,
                          double* E_grid, cudaStream_t s) {
     const int M = kp.M, Mh = M / 2 + 1;
-    const int nch = (Mh + kFastKC - 1) / kFastKC;
+    const int nch = (Mh + kXpassKC - 1) / kXpassKC;
     const float2* tw = (const float2*)b.tw;
     const float2* C = (const float2*)b.cgrid;
     const int nsm = sm_count();
@@ -145,7 +145,7 @@ bool fast_slab_gather_ok(int M) {
 cudaError_t fast_grid_energy(const KParams<float>& kp, const FastBufs& b, double e_scale,
                              double* E_out, cudaStream_t s) {
     const int Mh = kp.M / 2 + 1;
-    const int nch = (Mh + kFastKC - 1) / kFastKC;
+    const int nch = (Mh + kXpassKC - 1) / kXpassKC;
     return launch_ex(k_grid_energy, 1, kThreads, 0, s, true,
                      (const double*)(b.partials + 5 * kMaxPartials), kp.M * nch, b.acc, e_scale,
                      E_out);
@@ -156,7 +156,7 @@ cudaError_t fast_gather_slab_P(const KParams<float>& kp, const FastBufs& b, floa
                                double* partials, unsigned* ticket, double e_scale, double* E_out,
                                const double* adj, cudaStream_t s) {
     const int M = kp.M, Mh = M / 2 + 1;
-    const int nch = (Mh + kFastKC - 1) / kFastKC;
+    const int nch = (Mh + kXpassKC - 1) / kXpassKC;
     const int nsm = sm_count();
     // at most ceil(2 (M + 1) / SMs) CTAs per SM, whatever else is resident
     // when the grid is scheduled early
@@ -196,7 +196,7 @@ cudaError_t fast_transform(const KParams<float>& kp, const FastBufs& b, double e
                            double* E_grid, cudaStream_t s, bool marks, void (*mark)(void*, int),
                            void* ctx, bool inverse) {
     const int M = kp.M, Mh = M / 2 + 1;
-    const int nch = (Mh + kFastKC - 1) / kFastKC;
+    const int nch = (Mh + kXpassKC - 1) / kXpassKC;
     const float2* tw = (const float2*)b.tw;
     float2* C = (float2*)b.cgrid;
     const int nsm = sm_count();
@@ -204,7 +204,7 @@ cudaError_t fast_transform(const KParams<float>& kp, const FastBufs& b, double e
     // 2-CTA clusters per x-slab when every CTA gets an SM of its own;
     // otherwise one CTA per slab (a cap of two CTAs per SM would let an early
     // placement pack them onto half the SMs)
-    const bool clusters = nsm > 0 && kSlabCL * (M + 1) <= nsm;
+    const bool clusters = slab_clusters(M);
     // at least half an SM's shared memory: one slab CTA per SM, whatever else
     // is resident when the grid is scheduled early
     const size_t slab = std::max(slab_smem_bytes(M), kSlabSmemFloor);
