@@ -734,8 +734,11 @@ __device__ __forceinline__ void gather_accum(const GatherPrep<T, P>& g, const T*
 
 // Single precision and P <= 8: at most 64 registers, so that four CTAs fit on
 // an SM (a bound of 48 for five makes the accumulation spill).
+#ifndef SE_GATHER_MINB
+#define SE_GATHER_MINB 4
+#endif
 template <typename T, int P>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 8) ? 4 : 1)
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 8) ? SE_GATHER_MINB : 1)
 k_gather(const v4_t<T>* __restrict__ sorted, const int* __restrict__ perm,
  const T* __restrict__ grid, T* __restrict__ phi, T* __restrict__ F,
  const KParams<T> kp, double* __restrict__ partials, unsigned* ticket, Acc* acc,
