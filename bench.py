@@ -580,8 +580,11 @@ def finish_single(args, se, torch, res, K, W, flush, headline):
 
 
 def e2e(se, torch, x, q, w, prec, K, cfg):
-    """Host buffers through se_energy_force_host: H2D of xyz and q, the
-    evaluation, D2H of F, phi and E, every step."""
+    """Host buffers through se_energy_force_host, every step: xyz and q from
+    page-locked host memory to the GPU, the evaluation, F, phi and E back to
+    host memory.  With these (mapped) buffers the library's kernels read the
+    inputs and write the outputs in host memory directly over the host link,
+    as one CUDA graph; the bytes counted are those that cross the link."""
     N = len(q)
     plan = se.Plan(N, w["L"], w["xi"], w["M"], w["P"], precision=prec)
     if prec != "fp64":
@@ -603,7 +606,8 @@ def e2e(se, torch, x, q, w, prec, K, cfg):
     es = hx.element_size()
     return {"value": r4(K / (t1 - t0)), "unit": "evals/s", "steps": K,
             "h2d_bytes_per_step": N * 4 * es, "d2h_bytes_per_step": N * 4 * es + 8 + 32,
-            "timing": "host wall clock around each synchronous call"}
+            "timing": "host wall clock around each synchronous call",
+            "transfer": "kernels read and write the pinned, mapped host buffers directly"}
 
 
 def autograd_timing(se, torch, x, q, w, prec, plan, xd, qd, K, flush):

@@ -200,8 +200,14 @@ int se_plan_set_graph(se_plan *plan, int enable);
 
 /* As se_energy_force but every array is in HOST memory: the call copies xyz
  * and q to the device, evaluates, and copies F, phi and E back before it
- * returns.  Host arrays in page-locked memory make the copies asynchronous
- * with respect to other host work. */
+ * returns.  When every host array is page-locked and mapped into the
+ * device's address space (cudaMallocHost, cudaHostAlloc, or cudaHostRegister
+ * with cudaHostRegisterMapped) and graphs are enabled (se_plan_set_graph),
+ * the kernels read xyz and q and write F and phi in host memory directly
+ * (over the host link, no staging copies), and the evaluation is one CUDA
+ * graph, captured at the first call and again whenever a host pointer or the
+ * prefactor changes, then replayed; otherwise the arrays are copied through
+ * device staging buffers one by one.  The results are the same either way. */
 int se_energy_force_host(se_plan *plan, const void *xyz, const void *q,
                          double *E, void *F, void *phi);
 

@@ -107,6 +107,14 @@ struct se_plan {
     cudaGraphExec_t gexec = nullptr;
     const void* gkey[5] = {};
     double gkey_kc = 0.0;
+    // se_energy_force_host with page-locked, mapped host buffers: one CUDA
+    // graph in which the kernels read and write the host buffers directly,
+    // replayed while the host pointers match; the reduction record comes back
+    // to acc_host (pinned)
+    cudaGraphExec_t hexec = nullptr;
+    const void* hkey[4] = {};
+    double hkey_kc = 0.0;
+    Acc* acc_host = nullptr;
 };
 
 namespace {
@@ -211,6 +219,8 @@ void derive(se_plan* p) {
 void drop_graph(se_plan* p) {
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     p->gexec = nullptr;
+    if (p->hexec) cudaGraphExecDestroy(p->hexec);
+    p->hexec = nullptr;
 }
 
 void release_device(se_plan* p) {
@@ -237,6 +247,8 @@ void release_device(se_plan* p) {
     p->tickets = nullptr;
     p->acc = nullptr;
     p->h_xyz = p->h_q = p->h_F = p->h_phi = nullptr;
+    if (p->acc_host) cudaFreeHost(p->acc_host);
+    p->acc_host = nullptr;
     p->ready = false;
     p->ready_prec = -1;
     p->ready_force = -1;
@@ -676,6 +688,99 @@ int graph_evaluate(se_plan* p, const void* xyz, const void* q, void* F, void* ph
     return SE_OK;
 }
 
+// The device address of page-locked host memory that is mapped into the
+// device's address space (cudaMallocHost / cudaHostAlloc, or cudaHostRegister
+// with cudaHostRegisterMapped), else NULL.  *ok: NULL in, or mapped.
+const void* mapped_host(const void* ptr, bool* ok) {
+    if (!ptr) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        *ok = false;
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) {
+        *ok = false;
+        return nullptr;
+    }
+    return a.devicePointer;
+}
+
+// se_energy_force_host as one CUDA graph when every host array is page-locked
+// and mapped: the kernels read xyz and q straight from host memory (the first
+// kernel, over the host link) and the gather writes F and phi straight into
+// it, so the only copy is the reduction record into the plan's pinned
+// acc_host.  Captured the first time (and whenever a host pointer or the
+// prefactor changes) and replayed; the caller synchronises.
+// SE_ERR_UNSUPPORTED when the graph cannot be used (the caller then copies and
+// launches directly).
+int graph_evaluate_host(se_plan* p, const void* xyz, const void* q, void* F, void* phi) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(p->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return SE_ERR_UNSUPPORTED;
+    const void* key[4] = {xyz, q, F, phi};
+    bool match = p->hexec && p->hkey_kc == p->kc;
+    for (int i = 0; i < 4 && match; ++i) match = key[i] == p->hkey[i];
+    if (!match) {
+        if (p->hexec) cudaGraphExecDestroy(p->hexec);
+        p->hexec = nullptr;
+        bool ok = true;
+        const void* dx = mapped_host(xyz, &ok);
+        const void* dq = mapped_host(q, &ok);
+        void* dF = const_cast<void*>(mapped_host(F, &ok));
+        void* dphi = const_cast<void*>(mapped_host(phi, &ok));
+        if (!ok) return SE_ERR_UNSUPPORTED;
+        if (!p->acc_host && cudaMallocHost((void**)&p->acc_host, sizeof(Acc)) != cudaSuccess) {
+            cudaGetLastError();
+            p->acc_host = nullptr;
+            return SE_ERR_UNSUPPORTED;
+        }
+        if (!p->cap_stream)
+            SE_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+        if (!p->spread_clean) {
+            const size_t M3 = (size_t)p->M * p->M * p->M;
+            if (p->variant >= 3)
+                SE_CUDA(cudaMemsetAsync(p->g64, 0, M3 * sizeof(long long), p->stream));
+            else
+                SE_CUDA(cudaMemsetAsync(p->grid_spread, 0, M3 * tsize(p->prec), p->stream));
+            p->spread_clean = true;
+        }
+        SE_CUDA(cudaStreamSynchronize(p->stream));
+        cudaStream_t user = p->stream;
+        p->stream = p->cap_stream;
+        const bool timing = p->timing;
+        p->timing = false;
+        cudaGraph_t g = nullptr;
+        int rc = check_cuda(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+        if (rc == SE_OK) {
+            rc = evaluate(p, dx, dq, dF, dphi, p->dE);
+            if (rc == SE_OK)
+                rc = check_cuda(cudaMemcpyAsync(p->acc_host, p->acc, sizeof(Acc), cudaMemcpyDeviceToHost,
+                                                p->stream));
+            cudaError_t e = cudaStreamEndCapture(p->cap_stream, &g);
+            if (rc == SE_OK && e != cudaSuccess) rc = SE_ERR_CUDA;
+        }
+        p->stream = user;
+        p->timing = timing;
+        if (rc == SE_OK && cudaGraphInstantiate(&p->hexec, g, 0) != cudaSuccess) {
+            p->hexec = nullptr;
+            rc = SE_ERR_CUDA;
+        }
+        if (g) cudaGraphDestroy(g);
+        if (rc != SE_OK) {
+            cudaGetLastError();
+            p->hexec = nullptr;
+            return rc;
+        }
+        for (int i = 0; i < 4; ++i) p->hkey[i] = key[i];
+        p->hkey_kc = p->kc;
+    }
+    SE_CUDA(cudaGraphLaunch(p->hexec, p->stream));
+    p->spread_clean = true;
+    p->have_spread = p->have_scale = true;
+    return SE_OK;
+}
+
 // evaluate() through the graph when allowed, else by direct launches.
 int run_eval(se_plan* p, const void* xyz, const void* q, void* F, void* phi, double* dE) {
     if (p->use_graph && !p->timing) {
@@ -890,6 +995,18 @@ int se_energy_force_host(se_plan* p, const void* xyz, const void* q, double* E, 
         if (rc == SE_OK) rc = dalloc(&p->h_F, 3 * N * ts);
         if (rc == SE_OK) rc = dalloc(&p->h_phi, N * ts);
         if (rc != SE_OK) return rc;
+    }
+    // page-locked, mapped host buffers: the evaluation reads and writes them
+    // directly, as one replayed graph
+    if (N > 0 && p->use_graph && !p->timing) {
+        const int rc = graph_evaluate_host(p, xyz, q, F, phi);
+        if (rc == SE_OK) {
+            SE_CUDA(cudaStreamSynchronize(p->stream));
+            const Acc a = *p->acc_host;
+            if (E) *E = energy_from_acc(p, a, !F && !phi);
+            return status_from_acc(a);
+        }
+        if (rc != SE_ERR_UNSUPPORTED) p->use_graph = false;   // capture failed: stop trying
     }
     if (N > 0) {
         SE_CUDA(cudaMemcpyAsync(p->h_xyz, xyz, 3 * N * ts, cudaMemcpyHostToDevice, p->stream));

@@ -646,3 +646,31 @@ def test_fused_gather_is_order_independent():
     assert np.array_equal(F1.cpu().numpy(), F0[perm])
     assert np.array_equal(phi1.cpu().numpy(), phi0[perm])
     plan.close()
+
+
+def test_host_entry_point_graph_with_pinned_buffers():
+    """se_energy_force_host with page-locked host buffers runs copies and
+    evaluation as one replayed CUDA graph: the results equal the device entry
+    point's bitwise, over repeated calls, after the host buffers change
+    (recapture) and with pageable buffers in between (copies one by one)."""
+    x, q, w = systems.make("water-L6-M52-P8-fp32comp")
+    N = len(q)
+    plan = se.Plan(N, w["L"], w["xi"], w["M"], w["P"], precision="fp32")
+    E0, F0, phi0 = plan.energy_force(torch.tensor(x, device="cuda"), torch.tensor(q, device="cuda"))
+    F0, phi0 = F0.cpu().numpy(), phi0.cpu().numpy()
+    bufs = []
+    for _ in range(2):
+        hx = torch.tensor(x).pin_memory()
+        hq = torch.tensor(q).pin_memory()
+        hF = torch.full((N, 3), float("nan")).pin_memory()
+        hphi = torch.full((N,), float("nan")).pin_memory()
+        bufs.append((hx, hq, hF, hphi))
+    for i in (0, 0, 1, 0):
+        hx, hq, hF, hphi = bufs[i]
+        hF.fill_(float("nan"))
+        E = plan.energy_force_host_ptrs(hx.data_ptr(), hq.data_ptr(), hF.data_ptr(), hphi.data_ptr())
+        assert E == E0
+        assert np.array_equal(hF.numpy(), F0) and np.array_equal(hphi.numpy(), phi0)
+        Ep, Fp, phip = plan.energy_force_host(x, q)      # pageable numpy arrays
+        assert Ep == E0 and np.array_equal(Fp, F0) and np.array_equal(phip, phi0)
+    plan.close()
