@@ -1004,8 +1004,12 @@ __device__ __forceinline__ void slab_fwd_body(G* __restrict__ grid, float2* __re
     }
     __syncthreads();
     SE_STAMP(3, 2);
-    // z, real to complex: X(j = z, c = y) = S[y][z]  ->  T[kz][y]
-    dft_r2c<2, 2>(S, 1, SP, T, SP, 1, M, Mh, M, tw, M);
+    // z, real to complex: X(j = z, c = y) = S[y][z]  ->  T[kz][y] (through Z
+    // and the dead S when M/2 factors)
+    if (dft_half_ok(M))
+        dft_r2c_half<2, 2>(S, 1, SP, T, SP, 1, M, Z, reinterpret_cast<float2*>(S), tw, M);
+    else
+        dft_r2c<2, 2>(S, 1, SP, T, SP, 1, M, Mh, M, tw, M);
     __syncthreads();
     SE_STAMP(3, 3);
     // y forward: X(j = y, c = kz) = T[kz][y]  ->  C[x][ky][kz]
@@ -1149,16 +1153,22 @@ __device__ __forceinline__ void slab_inv_body(const float2* __restrict__ C, floa
     __syncthreads();
     SE_STAMP(5, 2);
     const FDiv fM = fdiv_of(M);
-    for (int e = threadIdx.x; e < Mh * M; e += blockDim.x) {
-        const int kz = fdiv(e, fM), y = e - kz * M;
-        if (kz != 0 && 2 * kz != M) {
-            float2 v = T[kz * SP + y];
-            T[kz * SP + y] = make_float2(2.f * v.x, 2.f * v.y);
+    if (dft_half_ok(M)) {
+        // z complex to real through Z and S (the Hermitian symmetry of the
+        // half-length form takes the place of the weights)
+        dft_c2r_half<2, 2>(T, SP, 1, S, 1, SP, M, Z, reinterpret_cast<float2*>(S), tw, M, 1.0f);
+    } else {
+        for (int e = threadIdx.x; e < Mh * M; e += blockDim.x) {
+            const int kz = fdiv(e, fM), y = e - kz * M;
+            if (kz != 0 && 2 * kz != M) {
+                float2 v = T[kz * SP + y];
+                T[kz * SP + y] = make_float2(2.f * v.x, 2.f * v.y);
+            }
         }
+        __syncthreads();
+        // z complex to real: X(j = kz, c = y) = T[kz][y]  ->  S[y][z]
+        dft_c2r<2, 2>(T, SP, 1, S, 1, SP, Mh, M, M, tw, M);
     }
-    __syncthreads();
-    // z complex to real: X(j = kz, c = y) = T[kz][y]  ->  S[y][z]
-    dft_c2r<2, 2>(T, SP, 1, S, 1, SP, Mh, M, M, tw, M);
     __syncthreads();
     SE_STAMP(5, 3);
     float* dst = R + (size_t)x * M * M;
@@ -1289,7 +1299,12 @@ k_slab_fwd_cl(long long* __restrict__ g64, float2* __restrict__ Cg,
     __syncthreads();
     SE_STAMP(3, 2);
     // z, real to complex, own rows: X(j = z, c = yl) = S[yl][z]  ->  T[kz][yl]
-    dft_r2c<kClTK, kClTC>(S, 1, SP, T, l.ry, 1, M, Mh, ny, tw, M);
+    // (through Z and the dead S when M/2 factors; X receives the partner's
+    // pushes meanwhile and is not touched)
+    if (dft_half_ok(M))
+        dft_r2c_half<kClTK, kClTC>(S, 1, SP, T, l.ry, 1, ny, Z, reinterpret_cast<float2*>(S), tw, M);
+    else
+        dft_r2c<kClTK, kClTC>(S, 1, SP, T, l.ry, 1, M, Mh, ny, tw, M);
     __syncthreads();
     // push: kz column k of these rows goes to the CTA owning k, X[k - k0'][y0 + yl]
     {
@@ -1390,7 +1405,11 @@ k_slab_inv_cl(const float2* __restrict__ Cg, float* __restrict__ R, const float2
     }
     clu.sync();   // every push has landed; no shared memory is read remotely afterwards
     // z complex to real, own rows: X(j = kz, c = yl) = X[kz][yl]  ->  S[yl][z]
-    dft_c2r<kClInvTK, kClInvTC>(X, l.ry, 1, S, 1, SP, Mh, M, ny, tw, M);
+    // (through Z and T when M/2 factors)
+    if (dft_half_ok(M))
+        dft_c2r_half<kClInvTK, kClInvTC>(X, l.ry, 1, S, 1, SP, ny, Z, T, tw, M, 0.5f);
+    else
+        dft_c2r<kClInvTK, kClInvTC>(X, l.ry, 1, S, 1, SP, Mh, M, ny, tw, M);
     __syncthreads();
     SE_STAMP(5, 3);
     float* dst = R + ((size_t)x * M + y0) * M;

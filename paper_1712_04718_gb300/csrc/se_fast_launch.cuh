@@ -103,10 +103,14 @@ cudaError_t fast_spread(const float* xyz, const float* q, const KParams<float>& 
     }
 }
 
-// 2-CTA clusters per x-slab when every CTA gets an SM of its own
+// 2-CTA clusters per x-slab when every CTA gets an SM of its own (build
+// with -DSE_SLAB_CL_PER_SM=n to allow n cluster CTAs per SM)
+#ifndef SE_SLAB_CL_PER_SM
+#define SE_SLAB_CL_PER_SM 1
+#endif
 inline bool slab_clusters(int M) {
     const int nsm = sm_count();
-    return nsm > 0 && 2 * (M + 1) <= nsm;
+    return nsm > 0 && 2 * (M + 1) <= SE_SLAB_CL_PER_SM * nsm;
 }
 
 cudaError_t fast_inverse(const KParams<float>& kp, const FastBufs& b, double e_scale,

@@ -108,6 +108,31 @@ def test_stage_parity_small(prec, M, P, tile, variant):
     assert abs(g["E_grid"] - r["E_grid"]) < 5 * tol * abs(r["E_grid"]), "E_grid"
 
 
+@pytest.mark.parametrize("M", [60, 72, 84])
+def test_stage_parity_half_length_real_dft(M):
+    """Grids where the z transforms of the single-precision pipeline run as
+    complex transforms of length M/2 (factored 5 x 6, 6 x 6, 6 x 7): M = 60
+    and 72 on 2-CTA clusters, M = 84 one CTA per x-slab (on 152 SMs); the
+    scaled grid goes through the forward and the inverse real transforms.
+    Charges at the density of the water workloads (about 94 per nm^3): on a
+    grid four times sparser (1501 charges) the fixed-point spread grid's
+    worst element measured 2.6e-5 of its scale, above the 2e-5 bound."""
+    L, P = 4.0, 8
+    xi = min(3.5, math.sqrt(0.8 * 0.95 ** 2 * math.pi * M * M / (P * L * L)))
+    x, q = systems.uniform_charges(6001, L, seed=M, dtype=np.float32)
+    q = q.astype(np.float64)
+    q[-1] = -q[:-1].sum()
+    q = q.astype(np.float32)
+    g = run_gpu(x, q, L, xi, M, P, "fp32", grids=True, tile=8, spread_variant=3)
+    r = oracle_for(x, q, L, xi, M, P, "fp32", grids=True)
+    tol = TOL["fp32"]
+    assert_close(g["H"], r["H"], tol, label="spread grid")
+    assert_close(g["Ht"], r["Ht"], 5 * tol, label="scaled grid")
+    assert_close(g["phi"], r["phi"], 5 * tol, label="phi")
+    assert_close(g["F"], r["F"], 5 * tol, q=q, label="F")
+    assert abs(g["E"] - r["E"]) < 5 * tol * abs(r["E"]), "E"
+
+
 @pytest.mark.parametrize("M,P", [(32, 16), (32, 20), (40, 24), (36, 18)])
 def test_fp64_direct_and_tiled_spread_agree(M, P):
     """Both spreading variants give the oracle's grid (FP64)."""
