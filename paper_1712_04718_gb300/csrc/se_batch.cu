@@ -183,7 +183,7 @@ k_bslab_fwd(const long long* __restrict__ g64, float2* __restrict__ C, const flo
     const int s = slab_sys[blockIdx.x];
     const SysParams& sp = sys[s];
     slab_fwd_body(g64 + sp.g0, C + sp.c0, tw + sp.tw0, sp.kp.M, bacc[s].fx_inv,
-                  blockIdx.x - sp.slab0, sm);
+                  blockIdx.x - sp.slab0, sm, SE_DFT_HALF_BATCH_R4);
 }
 
 __global__ void __launch_bounds__(256)
@@ -210,7 +210,8 @@ k_bslab_inv(const float2* __restrict__ C, float* __restrict__ R, const float2* _
     extern __shared__ __align__(16) unsigned char sm[];
     const int s = slab_sys[blockIdx.x];
     const SysParams& sp = sys[s];
-    slab_inv_body(C + sp.c0, R + sp.g0, tw + sp.tw0, sp.kp.M, blockIdx.x - sp.slab0, sm);
+    slab_inv_body(C + sp.c0, R + sp.g0, tw + sp.tw0, sp.kp.M, blockIdx.x - sp.slab0, sm,
+                  SE_DFT_HALF_BATCH_R4);
 }
 
 template <int P>

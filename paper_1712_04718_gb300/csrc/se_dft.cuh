@@ -369,10 +369,16 @@ __device__ __forceinline__ void dft_c2r_half(const float2* X, int xj, int xc, fl
 #ifndef SE_DFT_HALF
 #define SE_DFT_HALF 1
 #endif
-__host__ __device__ inline bool dft_half_ok(int M) {
+constexpr int kDftHalfR4 = 11;   // the 2.75-fold cut, in quarters
+// Slab transforms of many systems at once (the ensemble) keep every SM busy:
+// there the saved terms pay at a smaller cut (build-time knob, in quarters).
+#ifndef SE_DFT_HALF_BATCH_R4
+#define SE_DFT_HALF_BATCH_R4 11
+#endif
+__host__ __device__ inline bool dft_half_ok(int M, int r4 = kDftHalfR4) {
     if (!SE_DFT_HALF || M % 2 != 0 || M < 8) return false;
     const int N = M / 2, N1 = dft_split(N);
-    return N1 > 1 && 8 * M * (M / 2 + 1) >= 44 * N * (N1 + N / N1);
+    return N1 > 1 && 2 * M * (M / 2 + 1) * 4 >= r4 * 4 * N * (N1 + N / N1);
 }
 
 }  // namespace se

@@ -938,6 +938,12 @@ k_fdirect(const float* __restrict__ xyz, const float* __restrict__ q, const KPar
 //   k_slab_inv  per x-slab: y inverse, then z complex-to-real (R[x][y][z])
 
 constexpr int kSlabThreads = 512;
+// threads of the single-system slab CTAs that take a whole x-slab each
+// (grids too large for one 2-CTA cluster per slab on every SM)
+#ifndef SE_SLAB_NC_THREADS
+#define SE_SLAB_NC_THREADS 1024
+#endif
+constexpr int kSlabNCThreads = SE_SLAB_NC_THREADS;
 
 __device__ __forceinline__ void load_twiddles(float2* tw, const float2* __restrict__ tw_g, int M) {
     for (int i = threadIdx.x; i < M; i += blockDim.x) tw[i] = tw_g[i];
@@ -967,7 +973,7 @@ __host__ __device__ inline size_t slab_smem_bytes(int M) {
 template <typename G, bool kClear = (sizeof(G) == sizeof(float))>
 __device__ __forceinline__ void slab_fwd_body(G* __restrict__ grid, float2* __restrict__ C,
                                               const float2* __restrict__ tw_g, int M, float inv,
-                                              int x, unsigned char* sm) {
+                                              int x, unsigned char* sm, int half_r4 = kDftHalfR4) {
     const int Mh = M / 2 + 1, SP = M + 1;
     float2* tw = reinterpret_cast<float2*>(sm);
     float* S = reinterpret_cast<float*>(sm + (size_t)M * sizeof(float2));
@@ -1006,7 +1012,7 @@ __device__ __forceinline__ void slab_fwd_body(G* __restrict__ grid, float2* __re
     SE_STAMP(3, 2);
     // z, real to complex: X(j = z, c = y) = S[y][z]  ->  T[kz][y] (through Z
     // and the dead S when M/2 factors)
-    if (dft_half_ok(M))
+    if (dft_half_ok(M, half_r4))
         dft_r2c_half<2, 2>(S, 1, SP, T, SP, 1, M, Z, reinterpret_cast<float2*>(S), tw, M);
     else
         dft_r2c<2, 2>(S, 1, SP, T, SP, 1, M, Mh, M, tw, M);
@@ -1018,7 +1024,7 @@ __device__ __forceinline__ void slab_fwd_body(G* __restrict__ grid, float2* __re
 }
 
 #ifndef SE_BATCH_TU
-__global__ void __launch_bounds__(kSlabThreads)
+__global__ void __launch_bounds__(kSlabNCThreads)
 k_slab_fwd(long long* __restrict__ g64, float2* __restrict__ C,
            const float2* __restrict__ tw_g, int M, const Acc* __restrict__ acc) {
     SE_STAMP(3, 0);
@@ -1030,7 +1036,7 @@ k_slab_fwd(long long* __restrict__ g64, float2* __restrict__ C,
 }
 
 // the same on the float grid of the unsorted spread (cleared after reading)
-__global__ void __launch_bounds__(kSlabThreads)
+__global__ void __launch_bounds__(kSlabNCThreads)
 k_slab_fwd_f(float* __restrict__ grid, float2* __restrict__ C, const float2* __restrict__ tw_g,
              int M) {
     SE_STAMP(3, 0);
@@ -1123,7 +1129,7 @@ k_xpass(float2* __restrict__ C, const float2* __restrict__ tw_g, const float* __
 // Inverse 2-D transform (y, then z complex-to-real) of x-slab x into R.
 __device__ __forceinline__ void slab_inv_body(const float2* __restrict__ C, float* __restrict__ R,
                                               const float2* __restrict__ tw_g, int M, int x,
-                                              unsigned char* sm) {
+                                              unsigned char* sm, int half_r4 = kDftHalfR4) {
     const int Mh = M / 2 + 1, SP = M + 1;
     float2* tw = reinterpret_cast<float2*>(sm);
     float* S = reinterpret_cast<float*>(sm + (size_t)M * sizeof(float2));
@@ -1153,7 +1159,7 @@ __device__ __forceinline__ void slab_inv_body(const float2* __restrict__ C, floa
     __syncthreads();
     SE_STAMP(5, 2);
     const FDiv fM = fdiv_of(M);
-    if (dft_half_ok(M)) {
+    if (dft_half_ok(M, half_r4)) {
         // z complex to real through Z and S (the Hermitian symmetry of the
         // half-length form takes the place of the weights)
         dft_c2r_half<2, 2>(T, SP, 1, S, 1, SP, M, Z, reinterpret_cast<float2*>(S), tw, M, 1.0f);
@@ -1182,7 +1188,7 @@ __device__ __forceinline__ void slab_inv_body(const float2* __restrict__ C, floa
 #ifndef SE_BATCH_TU
 // CTAs 0..M-1: the inverse slab transforms; CTA M: the grid energy from the
 // x pass's nparts partials (acc->e_grid and, scaled, *E_out).
-__global__ void __launch_bounds__(kSlabThreads)
+__global__ void __launch_bounds__(kSlabNCThreads)
 k_slab_inv(const float2* __restrict__ C, float* __restrict__ R, const float2* __restrict__ tw_g,
            int M, const double* __restrict__ xparts, int nparts, Acc* acc, double e_scale,
            double* E_out) {

@@ -125,7 +125,7 @@ cudaError_t fast_inverse(const KParams<float>& kp, const FastBufs& b, double e_s
         const size_t slab = std::max(slab_smem_bytes(M), kSlabSmemFloor);
         e = cudaFuncSetAttribute(k_slab_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab);
         if (e != cudaSuccess) return e;
-        return launch_ex(k_slab_inv, M + 1, kSlabThreads, slab, s, true, C, b.rgrid, tw, M,
+        return launch_ex(k_slab_inv, M + 1, kSlabNCThreads, slab, s, true, C, b.rgrid, tw, M,
                          (const double*)(b.partials + 5 * kMaxPartials), M * nch, b.acc, e_scale,
                          E_grid);
     }
@@ -216,11 +216,11 @@ cudaError_t fast_transform(const KParams<float>& kp, const FastBufs& b, double e
         if (b.unsorted) {
             e = cudaFuncSetAttribute(k_slab_fwd_f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab);
             if (e != cudaSuccess) return e;
-            e = launch_ex(k_slab_fwd_f, M, kSlabThreads, slab, s, true, (float*)b.g64, C, tw, M);
+            e = launch_ex(k_slab_fwd_f, M, kSlabNCThreads, slab, s, true, (float*)b.g64, C, tw, M);
         } else {
             e = cudaFuncSetAttribute(k_slab_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab);
             if (e != cudaSuccess) return e;
-            e = launch_ex(k_slab_fwd, M, kSlabThreads, slab, s, true, b.g64, C, tw, M,
+            e = launch_ex(k_slab_fwd, M, kSlabNCThreads, slab, s, true, b.g64, C, tw, M,
                           (const Acc*)b.acc);
         }
     } else {
