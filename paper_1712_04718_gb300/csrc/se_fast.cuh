@@ -970,7 +970,9 @@ __host__ __device__ inline size_t slab_smem_bytes(int M) {
 // Forward 2-D transform (z real-to-complex, then y) of x-slab x.  The input
 // is the fixed-point grid (long long, scaled by inv), or the float grid of
 // the unsorted spread (float), which is cleared after it is read.
-template <typename G, bool kClear = (sizeof(G) == sizeof(float))>
+// HM: the z transform's form, 0 direct, 1 half-length, 2 chosen at run time
+// (dft_half_ok with the threshold half_r4: the ensemble's many grid sizes).
+template <typename G, bool kClear = (sizeof(G) == sizeof(float)), int HM = 2>
 __device__ __forceinline__ void slab_fwd_body(G* __restrict__ grid, float2* __restrict__ C,
                                               const float2* __restrict__ tw_g, int M, float inv,
                                               int x, unsigned char* sm, int half_r4 = kDftHalfR4) {
@@ -1012,7 +1014,7 @@ __device__ __forceinline__ void slab_fwd_body(G* __restrict__ grid, float2* __re
     SE_STAMP(3, 2);
     // z, real to complex: X(j = z, c = y) = S[y][z]  ->  T[kz][y] (through Z
     // and the dead S when M/2 factors)
-    if (dft_half_ok(M, half_r4))
+    if (HM == 1 || (HM == 2 && dft_half_ok(M, half_r4)))
         dft_r2c_half<2, 2>(S, 1, SP, T, SP, 1, M, Z, reinterpret_cast<float2*>(S), tw, M);
     else
         dft_r2c<2, 2>(S, 1, SP, T, SP, 1, M, Mh, M, tw, M);
@@ -1024,6 +1026,7 @@ __device__ __forceinline__ void slab_fwd_body(G* __restrict__ grid, float2* __re
 }
 
 #ifndef SE_BATCH_TU
+template <bool kHalf>
 __global__ void __launch_bounds__(kSlabNCThreads)
 k_slab_fwd(long long* __restrict__ g64, float2* __restrict__ C,
            const float2* __restrict__ tw_g, int M, const Acc* __restrict__ acc) {
@@ -1032,10 +1035,11 @@ k_slab_fwd(long long* __restrict__ g64, float2* __restrict__ C,
     pdl_launch_next();
     SE_STAMP(3, 1);
     extern __shared__ __align__(16) unsigned char sm[];
-    slab_fwd_body<long long, true>(g64, C, tw_g, M, acc->fx_inv, blockIdx.x, sm);   // clears the grid
+    slab_fwd_body<long long, true, kHalf ? 1 : 0>(g64, C, tw_g, M, acc->fx_inv, blockIdx.x, sm);   // clears the grid
 }
 
 // the same on the float grid of the unsorted spread (cleared after reading)
+template <bool kHalf>
 __global__ void __launch_bounds__(kSlabNCThreads)
 k_slab_fwd_f(float* __restrict__ grid, float2* __restrict__ C, const float2* __restrict__ tw_g,
              int M) {
@@ -1044,7 +1048,7 @@ k_slab_fwd_f(float* __restrict__ grid, float2* __restrict__ C, const float2* __r
     pdl_launch_next();
     SE_STAMP(3, 1);
     extern __shared__ __align__(16) unsigned char sm[];
-    slab_fwd_body(grid, C, tw_g, M, 1.0f, blockIdx.x, sm);
+    slab_fwd_body<float, true, kHalf ? 1 : 0>(grid, C, tw_g, M, 1.0f, blockIdx.x, sm);
 }
 #endif  // SE_BATCH_TU
 
@@ -1126,7 +1130,9 @@ k_xpass(float2* __restrict__ C, const float2* __restrict__ tw_g, const float* __
 }
 #endif  // SE_BATCH_TU
 
-// Inverse 2-D transform (y, then z complex-to-real) of x-slab x into R.
+// Inverse 2-D transform (y, then z complex-to-real) of x-slab x into R (HM
+// as for slab_fwd_body).
+template <int HM = 2>
 __device__ __forceinline__ void slab_inv_body(const float2* __restrict__ C, float* __restrict__ R,
                                               const float2* __restrict__ tw_g, int M, int x,
                                               unsigned char* sm, int half_r4 = kDftHalfR4) {
@@ -1159,7 +1165,7 @@ __device__ __forceinline__ void slab_inv_body(const float2* __restrict__ C, floa
     __syncthreads();
     SE_STAMP(5, 2);
     const FDiv fM = fdiv_of(M);
-    if (dft_half_ok(M, half_r4)) {
+    if (HM == 1 || (HM == 2 && dft_half_ok(M, half_r4))) {
         // z complex to real through Z and S (the Hermitian symmetry of the
         // half-length form takes the place of the weights)
         dft_c2r_half<2, 2>(T, SP, 1, S, 1, SP, M, Z, reinterpret_cast<float2*>(S), tw, M, 1.0f);
@@ -1188,6 +1194,7 @@ __device__ __forceinline__ void slab_inv_body(const float2* __restrict__ C, floa
 #ifndef SE_BATCH_TU
 // CTAs 0..M-1: the inverse slab transforms; CTA M: the grid energy from the
 // x pass's nparts partials (acc->e_grid and, scaled, *E_out).
+template <bool kHalf>
 __global__ void __launch_bounds__(kSlabNCThreads)
 k_slab_inv(const float2* __restrict__ C, float* __restrict__ R, const float2* __restrict__ tw_g,
            int M, const double* __restrict__ xparts, int nparts, Acc* acc, double e_scale,
@@ -1207,7 +1214,7 @@ k_slab_inv(const float2* __restrict__ C, float* __restrict__ R, const float2* __
         return;
     }
     extern __shared__ __align__(16) unsigned char sm[];
-    slab_inv_body(C, R, tw_g, M, blockIdx.x, sm);
+    slab_inv_body<kHalf ? 1 : 0>(C, R, tw_g, M, blockIdx.x, sm);
 }
 #endif  // SE_BATCH_TU
 
@@ -1260,6 +1267,7 @@ __host__ __device__ inline SlabClLayout slabcl_layout(int M) {
 }
 
 #ifndef SE_BATCH_TU
+template <bool kHalf>
 __global__ void __launch_bounds__(kSlabThreads)
 k_slab_fwd_cl(long long* __restrict__ g64, float2* __restrict__ Cg,
               const float2* __restrict__ tw_g, int M, const Acc* __restrict__ acc) {
@@ -1307,7 +1315,7 @@ k_slab_fwd_cl(long long* __restrict__ g64, float2* __restrict__ Cg,
     // z, real to complex, own rows: X(j = z, c = yl) = S[yl][z]  ->  T[kz][yl]
     // (through Z and the dead S when M/2 factors; X receives the partner's
     // pushes meanwhile and is not touched)
-    if (dft_half_ok(M))
+    if constexpr (kHalf)
         dft_r2c_half<kClTK, kClTC>(S, 1, SP, T, l.ry, 1, ny, Z, reinterpret_cast<float2*>(S), tw, M);
     else
         dft_r2c<kClTK, kClTC>(S, 1, SP, T, l.ry, 1, M, Mh, ny, tw, M);
@@ -1333,6 +1341,7 @@ k_slab_fwd_cl(long long* __restrict__ g64, float2* __restrict__ Cg,
 
 // Clusters 0..M-1: inverse slab transforms; cluster M: the grid energy from
 // the x pass's nparts partials (acc->e_grid and, scaled, *E_out).
+template <bool kHalf>
 __global__ void __launch_bounds__(kSlabThreads)
 k_slab_inv_cl(const float2* __restrict__ Cg, float* __restrict__ R, const float2* __restrict__ tw_g,
               int M, const double* __restrict__ xparts, int nparts, Acc* acc, double e_scale,
@@ -1412,7 +1421,7 @@ k_slab_inv_cl(const float2* __restrict__ Cg, float* __restrict__ R, const float2
     clu.sync();   // every push has landed; no shared memory is read remotely afterwards
     // z complex to real, own rows: X(j = kz, c = yl) = X[kz][yl]  ->  S[yl][z]
     // (through Z and T when M/2 factors)
-    if (dft_half_ok(M))
+    if constexpr (kHalf)
         dft_c2r_half<kClInvTK, kClInvTC>(X, l.ry, 1, S, 1, SP, ny, Z, T, tw, M, 0.5f);
     else
         dft_c2r<kClInvTK, kClInvTC>(X, l.ry, 1, S, 1, SP, Mh, M, ny, tw, M);

@@ -123,17 +123,19 @@ cudaError_t fast_inverse(const KParams<float>& kp, const FastBufs& b, double e_s
     cudaError_t e;
     if (!slab_clusters(M)) {
         const size_t slab = std::max(slab_smem_bytes(M), kSlabSmemFloor);
-        e = cudaFuncSetAttribute(k_slab_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab);
+        auto kinv = dft_half_ok(M) ? k_slab_inv<true> : k_slab_inv<false>;
+        e = cudaFuncSetAttribute(kinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab);
         if (e != cudaSuccess) return e;
-        return launch_ex(k_slab_inv, M + 1, kSlabNCThreads, slab, s, true, C, b.rgrid, tw, M,
+        return launch_ex(kinv, M + 1, kSlabNCThreads, slab, s, true, C, b.rgrid, tw, M,
                          (const double*)(b.partials + 5 * kMaxPartials), M * nch, b.acc, e_scale,
                          E_grid);
     }
     const int per_sm = nsm > 0 ? (kSlabCL * (M + 1) + nsm - 1) / nsm : 1;
     const size_t cl = smem_cap_per_sm(slabcl_layout(M).total, per_sm);
-    e = cudaFuncSetAttribute(k_slab_inv_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cl);
+    auto kinvcl = dft_half_ok(M) ? k_slab_inv_cl<true> : k_slab_inv_cl<false>;
+    e = cudaFuncSetAttribute(kinvcl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cl);
     if (e != cudaSuccess) return e;
-    return launch_cluster(k_slab_inv_cl, kSlabCL * (M + 1), kSlabThreads, cl, kSlabCL, s, true, C,
+    return launch_cluster(kinvcl, kSlabCL * (M + 1), kSlabThreads, cl, kSlabCL, s, true, C,
                           b.rgrid, tw, M, (const double*)(b.partials + 5 * kMaxPartials), M * nch,
                           b.acc, e_scale, E_grid);
 }
@@ -214,22 +216,25 @@ cudaError_t fast_transform(const KParams<float>& kp, const FastBufs& b, double e
     const size_t slab = std::max(slab_smem_bytes(M), kSlabSmemFloor);
     if (b.unsorted || !clusters) {
         if (b.unsorted) {
-            e = cudaFuncSetAttribute(k_slab_fwd_f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab);
+            auto kf = dft_half_ok(M) ? k_slab_fwd_f<true> : k_slab_fwd_f<false>;
+            e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab);
             if (e != cudaSuccess) return e;
-            e = launch_ex(k_slab_fwd_f, M, kSlabNCThreads, slab, s, true, (float*)b.g64, C, tw, M);
+            e = launch_ex(kf, M, kSlabNCThreads, slab, s, true, (float*)b.g64, C, tw, M);
         } else {
-            e = cudaFuncSetAttribute(k_slab_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab);
+            auto kfx = dft_half_ok(M) ? k_slab_fwd<true> : k_slab_fwd<false>;
+            e = cudaFuncSetAttribute(kfx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab);
             if (e != cudaSuccess) return e;
-            e = launch_ex(k_slab_fwd, M, kSlabNCThreads, slab, s, true, b.g64, C, tw, M,
+            e = launch_ex(kfx, M, kSlabNCThreads, slab, s, true, b.g64, C, tw, M,
                           (const Acc*)b.acc);
         }
     } else {
         // 2-CTA clusters per x-slab, at most ceil(2M / SMs) CTAs per SM
         const int per_sm = nsm > 0 ? (kSlabCL * M + nsm - 1) / nsm : 1;
         const size_t cl = smem_cap_per_sm(slabcl_layout(M).total, per_sm);
-        e = cudaFuncSetAttribute(k_slab_fwd_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cl);
+        auto kcl = dft_half_ok(M) ? k_slab_fwd_cl<true> : k_slab_fwd_cl<false>;
+        e = cudaFuncSetAttribute(kcl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cl);
         if (e != cudaSuccess) return e;
-        e = launch_cluster(k_slab_fwd_cl, kSlabCL * M, kSlabThreads, cl, kSlabCL, s, true,
+        e = launch_cluster(kcl, kSlabCL * M, kSlabThreads, cl, kSlabCL, s, true,
                            b.g64, C, tw, M, (const Acc*)b.acc);
     }
     if (e != cudaSuccess) return e;
