@@ -18,10 +18,14 @@
 // home cell stages its stencil in shared memory with the image shifts
 // applied (the cells' ranges fetched in parallel, offsets by a warp scan,
 // each staged particle located by binary search; in chunks when they do not
-// fit), and each home particle's candidate loop is split over S adjacent
-// lanes (S a power of two, S x home particles <= the CTA), reduced by
-// shuffles.  Every particle sums its own potential and
-// force: no atomics on the outputs.  The energy is a deterministic two-level
+// fit).  In single precision each thread holds three home particles and
+// tests every candidate it loads from shared memory against all three (one
+// shared load per three distance tests); the candidate loop of a set of home
+// particles is split over S adjacent lanes (S a power of two), reduced by
+// shuffles.  In double precision (one home particle per thread) the hits of
+// a particle's S lanes are queued in shared memory and shared out evenly
+// before the erfc terms.  Every particle sums its own potential and force:
+// no atomics on the outputs.  The energy is a deterministic two-level
 // reduction (last block).
 #include <cuda_runtime.h>
 #include <math.h>
@@ -199,6 +203,9 @@ __device__ __forceinline__ double block_sum_d(double v, double* sbuf) {
 // such a pair of cells), each a distinct periodic image since nc >= 2K+1.
 constexpr int kMaxStencil = 343;   // K <= 3
 constexpr int kPairThreads = 128;
+#ifndef SE_RS_R32
+#define SE_RS_R32 3   // home particles per thread, single precision
+#endif
 
 template <typename T>
 __global__ void __launch_bounds__(kPairThreads)
@@ -211,6 +218,8 @@ k_rs_pairs(const typename R4<T>::type* __restrict__ sorted, const int* __restric
     V* nb = reinterpret_cast<V*>(smem_raw);
     __shared__ int s_b0[kMaxStencil], s_off[kMaxStencil + 1];
     __shared__ unsigned char s_sh[kMaxStencil];   // image shift per axis: 0, 1 (-L), 2 (+L)
+    // hit queues of the double-precision sum: 32 S entries per set of lanes
+    __shared__ unsigned short s_q[sizeof(T) == 8 ? 32 * kPairThreads : 1];
     __shared__ double sbuf[32];
     __shared__ bool last;
     const int cid = blockIdx.x;
@@ -249,18 +258,38 @@ k_rs_pairs(const typename R4<T>::type* __restrict__ sorted, const int* __restric
     }
     __syncthreads();
     const int total = s_off[W3];
+    // kR home particles per thread (single precision: 3, so that every
+    // candidate loaded from shared memory is tested against three of them); S
+    // lanes per set of kR particles, S the largest power of two up to 32 with
+    // 2 S ceil(nh / kR) <= the block's threads
+    constexpr int kR = sizeof(T) == 4 ? SE_RS_R32 : 1;
+    const int nset = (nh + kR - 1) / kR;
     int S = 1;
-    while (S < 32 && 2 * S * nh <= (int)blockDim.x) S <<= 1;
-    const int per_pass = blockDim.x / S;
-    const int s = threadIdx.x % S;
+    while (S < 32 && 2 * S * nset <= (int)blockDim.x) S <<= 1;
+    const int sets = blockDim.x / S;
+    const int per_pass = sets * kR;
+    const int s = threadIdx.x % S, set = threadIdx.x / S;
+    // the S lanes of a set: aligned, adjacent lanes of one warp
+    const unsigned gmask = S == 32 ? 0xffffffffu
+                                   : ((1u << S) - 1u) << ((threadIdx.x & 31) & ~(S - 1));
     double e_loc = 0.0;
     for (int pass0 = 0; pass0 < nh; pass0 += per_pass) {
-        const int li = pass0 + threadIdx.x / S;
-        const bool act = li < nh;
-        V me;
-        me.x = me.y = me.z = me.w = T(0);
-        if (act) me = sorted[h0 + li];
-        T ph = T(0), fx = T(0), fy = T(0), fz = T(0);
+        int li[kR];
+        bool act[kR];
+        V me[kR];
+        T ph[kR], fx[kR], fy[kR], fz[kR];
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            li[r] = pass0 + set + r * sets;
+            act[r] = li[r] < nh;
+            if (act[r]) {
+                me[r] = sorted[h0 + li[r]];
+            } else {   // far from every candidate: no hits
+                me[r].x = me[r].y = me[r].z = T(1e18);
+                me[r].w = T(0);
+            }
+            ph[r] = fx[r] = fy[r] = fz[r] = T(0);
+        }
         for (int c0 = 0; c0 < total; c0 += cap) {
             const int filled = min(cap, total - c0);
             __syncthreads();
@@ -279,63 +308,109 @@ k_rs_pairs(const typename R4<T>::type* __restrict__ sorted, const int* __restric
                 nb[t] = v;
             }
             __syncthreads();
-            if (act) {
-                // 32 candidates per lane at a time: distance tests into a bit
-                // mask, then the erfc terms of the hits only (a warp then pays
-                // for its largest hit count, not for every candidate)
-                for (int j0 = s; j0 < filled; j0 += 32 * S) {
-                    unsigned mask = 0u;
+            if (!act[0]) continue;   // act[r] implies act[0]
+            // 32 candidates per lane at a time: distance tests into bit masks,
+            // then the erfc terms of the hits only
+            for (int jb = 0; jb < filled; jb += 32 * S) {   // uniform over the set
+                const int j0 = jb + s;
+                unsigned mask[kR];
+#pragma unroll
+                for (int r = 0; r < kR; ++r) mask[r] = 0u;
 #pragma unroll 8
-                    for (int b = 0; b < 32; ++b) {
-                        const int j = j0 + b * S;
-                        if (j < filled) {
-                            const V n = nb[j];
-                            const T dx = me.x - n.x, dy = me.y - n.y, dz = me.z - n.z;
+                for (int b = 0; b < 32; ++b) {
+                    const int j = j0 + b * S;
+                    if (j < filled) {
+                        const V n = nb[j];
+#pragma unroll
+                        for (int r = 0; r < kR; ++r) {
+                            const T dx = me[r].x - n.x, dy = me[r].y - n.y, dz = me[r].z - n.z;
                             const T r2 = dx * dx + dy * dy + dz * dz;
-                            if (r2 < rc2 && r2 > T(0)) mask |= 1u << b;
+                            if (r2 < rc2 && r2 > T(0)) mask[r] |= 1u << b;
                         }
                     }
-                    while (mask) {
-                        const int b = __ffs(mask) - 1;
-                        mask &= mask - 1u;
-                        const V n = nb[j0 + b * S];
-                        const T dx = me.x - n.x, dy = me.y - n.y, dz = me.z - n.z;
+                }
+                if constexpr (kR == 1) {
+                    // double: the hit terms dominate, so the set's hits are
+                    // queued in shared memory and shared out evenly (the set
+                    // pays for its mean hit count per lane, not its largest)
+                    unsigned short* qg = s_q + set * (32 * S);
+                    const int cnt = __popc(mask[0]);
+                    int pre = cnt;   // inclusive scan over the set's lanes
+                    for (int o = 1; o < S; o <<= 1) {
+                        const int y = __shfl_up_sync(gmask, pre, o, S);
+                        if (s >= o) pre += y;
+                    }
+                    const int tot = __shfl_sync(gmask, pre, S - 1, S);
+                    int w = pre - cnt;
+                    unsigned m = mask[0];
+                    while (m) {
+                        const int b = __ffs(m) - 1;
+                        m &= m - 1u;
+                        qg[w++] = (unsigned short)(j0 + b * S);
+                    }
+                    __syncwarp(gmask);
+                    for (int t = s; t < tot; t += S) {
+                        const V n = nb[qg[t]];
+                        const T dx = me[0].x - n.x, dy = me[0].y - n.y, dz = me[0].z - n.z;
                         const T r2 = dx * dx + dy * dy + dz * dz;
                         T ec, fr;
                         pair_terms(r2, rsqrtR(r2), xi, c2xi, ec, fr);
-                        ph += n.w * ec;
+                        ph[0] += n.w * ec;
                         const T f = n.w * fr;
-                        fx += f * dx;
-                        fy += f * dy;
-                        fz += f * dz;
+                        fx[0] += f * dx;
+                        fy[0] += f * dy;
+                        fz[0] += f * dz;
+                    }
+                    __syncwarp(gmask);   // the queue is rewritten by the next batch
+                } else {
+#pragma unroll
+                    for (int r = 0; r < kR; ++r) {
+                        unsigned m = mask[r];
+                        while (m) {
+                            const int b = __ffs(m) - 1;
+                            m &= m - 1u;
+                            const V n = nb[j0 + b * S];
+                            const T dx = me[r].x - n.x, dy = me[r].y - n.y, dz = me[r].z - n.z;
+                            const T r2 = dx * dx + dy * dy + dz * dz;
+                            T ec, fr;
+                            pair_terms(r2, rsqrtR(r2), xi, c2xi, ec, fr);
+                            ph[r] += n.w * ec;
+                            const T f = n.w * fr;
+                            fx[r] += f * dx;
+                            fy[r] += f * dy;
+                            fz[r] += f * dz;
+                        }
                     }
                 }
             }
         }
-        // sum over the S lanes of each particle (adjacent lanes, aligned groups)
-        for (int o = S >> 1; o > 0; o >>= 1) {
-            ph += __shfl_xor_sync(0xffffffffu, ph, o);
-            fx += __shfl_xor_sync(0xffffffffu, fx, o);
-            fy += __shfl_xor_sync(0xffffffffu, fy, o);
-            fz += __shfl_xor_sync(0xffffffffu, fz, o);
-        }
-        if (act && s == 0) {
-            const T pm = kc * (ph - c2xi * me.w);
-            const T fq = kc * me.w;
-            const int o = perm[h0 + li];
-            if (phi) phi[o] = accumulate ? phi[o] + pm : pm;
-            if (F) {
-                if (accumulate) {
-                    F[3 * o] += fq * fx;
-                    F[3 * o + 1] += fq * fy;
-                    F[3 * o + 2] += fq * fz;
-                } else {
-                    F[3 * o] = fq * fx;
-                    F[3 * o + 1] = fq * fy;
-                    F[3 * o + 2] = fq * fz;
-                }
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            // sum over the S lanes of the set (adjacent lanes, aligned groups)
+            for (int o = S >> 1; o > 0; o >>= 1) {
+                ph[r] += __shfl_xor_sync(0xffffffffu, ph[r], o);
+                fx[r] += __shfl_xor_sync(0xffffffffu, fx[r], o);
+                fy[r] += __shfl_xor_sync(0xffffffffu, fy[r], o);
+                fz[r] += __shfl_xor_sync(0xffffffffu, fz[r], o);
             }
-            e_loc += (double)me.w * (double)pm;
+            if (act[r] && s == 0) {
+                const T pm = kc * (ph[r] - c2xi * me[r].w);
+                const T fq = kc * me[r].w;
+                const int o = perm[h0 + li[r]];
+                if (phi) phi[o] = accumulate ? phi[o] + pm : pm;
+                if (F) {
+                    if (accumulate) {
+                        F[3 * o] += fq * fx[r];
+                        F[3 * o + 1] += fq * fy[r];
+                        F[3 * o + 2] += fq * fz[r];
+                    } else {
+                        F[3 * o] = fq * fx[r];
+                        F[3 * o + 1] = fq * fy[r];
+                        F[3 * o + 2] = fq * fz[r];
+                    }
+                }
+                e_loc += (double)me[r].w * (double)pm;
+            }
         }
     }
     const double r = block_sum_d(e_loc, sbuf);
