@@ -42,7 +42,10 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kMaxCellsPerDim = 40;     // at most 64 000 cells (one energy partial each)
-constexpr size_t kNbSmem = 32 * 1024;   // shared memory for staged neighbours
+#ifndef SE_RS_NB_KB
+#define SE_RS_NB_KB 32
+#endif
+constexpr size_t kNbSmem = SE_RS_NB_KB * 1024;   // shared memory for staged neighbours
 
 template <typename T> struct R4 { using type = se::v4_t<T>; };
 
@@ -202,7 +205,10 @@ __device__ __forceinline__ double block_sum_d(double v, double* sbuf) {
 // (cells of edge >= rc / K, so that every pair within rc has both ends in
 // such a pair of cells), each a distinct periodic image since nc >= 2K+1.
 constexpr int kMaxStencil = 343;   // K <= 3
-constexpr int kPairThreads = 128;
+#ifndef SE_RS_THREADS
+#define SE_RS_THREADS 192
+#endif
+constexpr int kPairThreads = SE_RS_THREADS;
 #ifndef SE_RS_R32
 #define SE_RS_R32 3   // home particles per thread, single precision
 #endif
