@@ -304,9 +304,9 @@ cudaError_t gather_pdl_P(const f4* sorted, const int* perm, const float* grid, f
                          Acc* acc, double e_scale, double* E_out, const double* adj,
                          cudaStream_t s) {
     constexpr int GPW = 32 / (P / pick_d(P));
-    const int gpb = (kThreads / 32) * GPW;
+    const int gpb = (gather_threads<float, P>() / 32) * GPW;
     const int blocks = std::max(1, std::min((kp.N + gpb - 1) / gpb, kMaxPartials));
-    return launch_ex(k_gather<float, P>, blocks, kThreads, 0, s, true, sorted, perm, grid, phi, F,
+    return launch_ex(k_gather<float, P>, blocks, gather_threads<float, P>(), 0, s, true, sorted, perm, grid, phi, F,
                      kp, partials, ticket, acc, e_scale, E_out, adj);
 }
 

@@ -737,8 +737,16 @@ __device__ __forceinline__ void gather_accum(const GatherPrep<T, P>& g, const T*
 #ifndef SE_GATHER_MINB
 #define SE_GATHER_MINB 4
 #endif
+#ifndef SE_GATHER_THREADS
+#define SE_GATHER_THREADS 256
+#endif
+// threads of a k_gather CTA (every launch of the instantiation uses it)
 template <typename T, int P>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 && P <= 8) ? SE_GATHER_MINB : 1)
+__host__ __device__ constexpr int gather_threads() {
+    return (sizeof(T) == 4 && P <= 8) ? SE_GATHER_THREADS : 256;
+}
+template <typename T, int P>
+__global__ void __launch_bounds__(gather_threads<T, P>(), (sizeof(T) == 4 && P <= 8) ? SE_GATHER_MINB : 1)
 k_gather(const v4_t<T>* __restrict__ sorted, const int* __restrict__ perm,
  const T* __restrict__ grid, T* __restrict__ phi, T* __restrict__ F,
  const KParams<T> kp, double* __restrict__ partials, unsigned* ticket, Acc* acc,

@@ -104,9 +104,9 @@ cudaError_t gather_P(const v4_t<T>* sorted, const int* perm, const T* grid, T* p
                      const KParams<T>& kp, double* partials, unsigned* ticket, Acc* acc,
                      double e_scale, double* E_out, const double* adj, cudaStream_t s) {
     constexpr int GPW = 32 / (P / pick_d(P));
-    const int gpb = (kThreads / 32) * GPW;
+    const int gpb = (gather_threads<T, P>() / 32) * GPW;
     const int blocks = std::max(1, std::min((kp.N + gpb - 1) / gpb, kMaxPartials));
-    k_gather<T, P><<<blocks, kThreads, 0, s>>>(sorted, perm, grid, phi, F, kp, partials, ticket,
+    k_gather<T, P><<<blocks, gather_threads<T, P>(), 0, s>>>(sorted, perm, grid, phi, F, kp, partials, ticket,
                                                acc, e_scale, E_out, adj);
     return cudaGetLastError();
 }
