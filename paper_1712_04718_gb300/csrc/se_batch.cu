@@ -173,7 +173,16 @@ k_bspread(const f4* __restrict__ sorted, const int* __restrict__ tile_start,
                    bacc[s].fx_scale, slab, tile, reinterpret_cast<unsigned*>(smem_raw), sE3);
 }
 
-__global__ void __launch_bounds__(kSlabThreads)
+// threads of the ensemble's slab CTAs (one x-slab of one system each):
+// 256 measured fastest for the 64-box water ensemble (0.821 ms per
+// evaluation against 0.851 at 512 and 0.954 at 1024; 128 as 256), the
+// slabs of many systems filling every SM at any size
+#ifndef SE_BSLAB_THREADS
+#define SE_BSLAB_THREADS 256
+#endif
+constexpr int kBSlabThreads = SE_BSLAB_THREADS;
+
+__global__ void __launch_bounds__(kBSlabThreads)
 k_bslab_fwd(const long long* __restrict__ g64, float2* __restrict__ C, const float2* __restrict__ tw,
             const SysParams* __restrict__ sys, const BAcc* __restrict__ bacc,
             const int* __restrict__ slab_sys) {
@@ -202,7 +211,7 @@ k_bxpass(float2* __restrict__ C, const float2* __restrict__ tw, const float* __r
     }
 }
 
-__global__ void __launch_bounds__(kSlabThreads)
+__global__ void __launch_bounds__(kBSlabThreads)
 k_bslab_inv(const float2* __restrict__ C, float* __restrict__ R, const float2* __restrict__ tw,
             const SysParams* __restrict__ sys, const int* __restrict__ slab_sys) {
     pdl_wait();
@@ -698,7 +707,7 @@ int batch_launch(se_batch* b, const float* xyz, const float* q, float* F, float*
     if (cudaFuncSetAttribute(se::k_bslab_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab) != cudaSuccess ||
         cudaFuncSetAttribute(se::k_bslab_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab) != cudaSuccess)
         return SE_ERR_CUDA;
-    e = se::launch_ex(se::k_bslab_fwd, b->Stot, se::kSlabThreads, slab, s, true, (const long long*)b->g64,
+    e = se::launch_ex(se::k_bslab_fwd, b->Stot, se::kBSlabThreads, slab, s, true, (const long long*)b->g64,
                       b->cgrid, (const float2*)b->tw, (const SysParams*)b->d_sys,
                       (const BAcc*)b->d_bacc, (const int*)b->slab_sys);
     if (e != cudaSuccess) return SE_ERR_CUDA;
@@ -708,7 +717,7 @@ int batch_launch(se_batch* b, const float* xyz, const float* q, float* F, float*
                       b->x_part);
     if (e != cudaSuccess) return SE_ERR_CUDA;
     mark(5);
-    e = se::launch_ex(se::k_bslab_inv, b->Stot, se::kSlabThreads, slab, s, true, (const float2*)b->cgrid,
+    e = se::launch_ex(se::k_bslab_inv, b->Stot, se::kBSlabThreads, slab, s, true, (const float2*)b->cgrid,
                       b->rgrid, (const float2*)b->tw, (const SysParams*)b->d_sys,
                       (const int*)b->slab_sys);
     if (e != cudaSuccess) return SE_ERR_CUDA;
