@@ -173,6 +173,14 @@ k_bspread(const f4* __restrict__ sorted, const int* __restrict__ tile_start,
                    bacc[s].fx_scale, slab, tile, reinterpret_cast<unsigned*>(smem_raw), sE3);
 }
 
+// kz columns per block of the ensemble's x pass: 12 measured fastest for
+// the 64-box water ensemble (its x pass 123 us against 137 at 8 and 193 at
+// 4; the shared-memory arrays of xpass_body bound it below 16)
+#ifndef SE_BX_KC
+#define SE_BX_KC 12
+#endif
+constexpr int kBxKC = SE_BX_KC;
+
 // threads of the ensemble's slab CTAs (one x-slab of one system each):
 // 256 measured fastest for the 64-box water ensemble (0.821 ms per
 // evaluation against 0.851 at 512 and 0.954 at 1024; 128 as 256), the
@@ -203,7 +211,7 @@ k_bxpass(float2* __restrict__ C, const float2* __restrict__ tw, const float* __r
     pdl_launch_next();
     const int s = x_sys[blockIdx.x];
     const SysParams& sp = sys[s];
-    const df2 e = xpass_body(C + sp.c0, tw + sp.tw0, green + sp.c0, sp.kp.M, sp.invM3,
+    const df2 e = xpass_body<kBxKC>(C + sp.c0, tw + sp.tw0, green + sp.c0, sp.kp.M, sp.invM3,
                              blockIdx.x - sp.x0);
     if (threadIdx.x == 0) {
         x_part[2 * blockIdx.x] = e.hi;
@@ -484,7 +492,7 @@ int build_tables(se_batch* b) {
         for (int a = 0; a < se::kMaxP; ++a) kp.E3[a] = (float)kd.E3[a];
         if (kp.ntiles > se::kScanLimit) return SE_ERR_UNSUPPORTED;
         const int M = b->M[s], Mh = M / 2 + 1;
-        const int nch = (Mh + se::kFastKC - 1) / se::kFastKC;
+        const int nch = (Mh + se::kBxKC - 1) / se::kBxKC;
         SysParams& q = sp[s];
         q.kp = kp;
         q.p0 = p0;
@@ -554,7 +562,7 @@ int prepare_batch(se_batch* b) {
         Ctot += M * M * Mh;
         TW += (int)M;
         slabs += (int)M;
-        xs += (int)(M * ((Mh + se::kFastKC - 1) / se::kFastKC));
+        xs += (int)(M * ((Mh + se::kBxKC - 1) / se::kBxKC));
         maxM = std::max(maxM, (int)M);
     }
     b->Ntot = Ntot;
